@@ -1,0 +1,295 @@
+"""Python handle on the plain C oracle (``jag_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  Nothing here imports the
+CUDA package; arrays come from the seeded generators and are passed as plain
+numpy buffers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jag_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libjag_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+K_NONE, K_LABEL, K_RANGE_I32, K_RANGE_F32, K_SUBSET, K_BOOL = range(6)
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-pthread", "-Wall", "-Wno-unused-function"]
+
+
+def compile_lib(force: bool = False) -> str:
+    """Compile the oracle with gcc (no CUDA, no shared headers)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Index(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("x", C.c_void_p),
+                ("a_i32", C.c_void_p), ("a_f32", C.c_void_p), ("a_mask", C.c_void_p),
+                ("dist_a", C.c_int32), ("R", C.c_int32), ("graph", C.c_void_p),
+                ("entry", C.c_int64)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(compile_lib())
+            P, I64, I32, F32, U64 = C.c_void_p, C.c_int64, C.c_int, C.c_float, C.c_uint64
+            sig = {
+                "orc_dist_canon": (F32, [P, P, I64]),
+                "orc_dist_f64": (C.c_double, [P, P, I64]),
+                "orc_bool_lut": (I32, [U64, P, P]),
+                "orc_brute_force": (None, [P, P, P, P, I64, I32, P, P, P, P, I32]),
+                "orc_query": (I32, [P, P, P, P, I64, I32, I32, I32, I64, I64, P, P, P, I32]),
+                "orc_query_lists": (None, [P, P, P, P, I64, I32, P, P, P, P, I32]),
+                "orc_medoid": (I64, [P, I64, I64]),
+                "orc_sm64": (U64, [U64, U64]),
+                "orc_thresholds": (None, [P, P, I32, I32, U64, P, I32]),
+                "orc_build": (I32, [P, P, I32, I32, F32, I32]),
+                "orc_joint_prune": (I32, [P, I64, P, P, I32, P, I32, F32, P]),
+                "orc_build_search": (I64, [P, I64, C.c_uint32, I32, P, P, I64]),
+                "orc_dist_F_batch": (None, [P, P, P, P, I64, P]),
+                "orc_g_batch": (None, [P, P, P, P, I64, P]),
+                "orc_dist_canon_batch": (None, [P, P, I64, I64, P]),
+                "orc_route": (I32, [P, P, P, I64, I64, P]),
+                "orc_count_passing": (I64, [P, P, P]),
+                "orc_dist_A": (C.c_uint32, [P, I64, I64]),
+                "orc_capped": (C.c_uint32, [I32, C.c_uint32, C.c_uint32]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _c(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def alpha2_of(alpha: float) -> float:
+    """fp32 value of alpha^2, computed in double and rounded once."""
+    return float(np.float32(float(alpha) * float(alpha)))
+
+
+class Index:
+    """Base vectors, attributes and (optionally) a graph, as the oracle sees them."""
+
+    def __init__(self, x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=K_RANGE_I32,
+                 R=32, graph=None, entry=0):
+        self.x = _c(x, np.float32)
+        self.attr_i32 = _c(attr_i32, np.int32)
+        self.attr_f32 = _c(attr_f32, np.float32)
+        self.attr_mask = _c(attr_mask, np.uint64)
+        n, d = self.x.shape
+        self.R = int(R)
+        self.graph = (np.full((n, self.R), -1, np.int32) if graph is None
+                      else np.ascontiguousarray(graph, dtype=np.int32))
+        self.s = _Index(n, d, _p(self.x), _p(self.attr_i32), _p(self.attr_f32),
+                        _p(self.attr_mask), int(dist_a), self.R, _p(self.graph), int(entry))
+
+    @classmethod
+    def from_workload(cls, w, R=32, graph=None, entry=0):
+        return cls(w.x, w.attr_i32, w.attr_f32, w.attr_mask, w.dist_a, R, graph, entry)
+
+    @property
+    def n(self):
+        return self.s.n
+
+    @property
+    def d(self):
+        return self.s.d
+
+    @property
+    def entry(self):
+        return self.s.entry
+
+    @entry.setter
+    def entry(self, v):
+        self.s.entry = int(v)
+
+    def ref(self):
+        return C.byref(self.s)
+
+
+def default_threads():
+    return max(1, os.cpu_count() or 1)
+
+
+def dist_canon(q, x):
+    q = _c(q, np.float32)
+    x = _c(x, np.float32)
+    return float(lib().orc_dist_canon(_p(q), _p(x), q.shape[-1]))
+
+
+def dist_canon_rows(q, x):
+    q = _c(np.atleast_2d(q), np.float32)
+    x = _c(np.atleast_2d(x), np.float32)
+    out = np.empty(q.shape[0], np.float32)
+    lib().orc_dist_canon_batch(_p(q), _p(x), q.shape[0], q.shape[1], _p(out))
+    return out
+
+
+def dist_f64(q, x):
+    q = _c(q, np.float32)
+    x = _c(x, np.float32)
+    return float(lib().orc_dist_f64(_p(q), _p(x), q.shape[-1]))
+
+
+def bool_lut(vars_mask: int, table_bytes: np.ndarray):
+    m = bin(vars_mask).count("1")
+    lut = np.empty(1 << m, np.uint8)
+    tb = _c(table_bytes, np.uint8)
+    sat = lib().orc_bool_lut(vars_mask, _p(tb), _p(lut))
+    return lut, bool(sat)
+
+
+def brute_force(ix: Index, q, filters, aux, k, with_f64=True, nthreads=None):
+    q = _c(q, np.float32)
+    nq = q.shape[0]
+    f = np.ascontiguousarray(filters)
+    aux = _c(aux, np.uint8)
+    ids = np.empty((nq, k), np.int32)
+    d32 = np.empty((nq, k), np.float32)
+    d64 = np.empty((nq, k), np.float64) if with_f64 else None
+    npass = np.empty(nq, np.int64)
+    lib().orc_brute_force(ix.ref(), _p(q), _p(f), _p(aux), nq, k, _p(ids), _p(d32), _p(d64),
+                          _p(npass), nthreads or default_threads())
+    return ids, d32, d64, npass
+
+
+def query(ix: Index, q, filters, aux, k, ls, literal=False, s0=0, scan_cap=32768, nthreads=None):
+    """Query (Algorithm 2) for a batch; returns ids, dists, counters[nq,4] =
+    (hops, first-seen neighbours, distance computations, routed to scan)."""
+    q = _c(q, np.float32)
+    nq = q.shape[0]
+    f = np.ascontiguousarray(filters)
+    aux = _c(aux, np.uint8)
+    ids = np.empty((nq, k), np.int32)
+    dist = np.empty((nq, k), np.float32)
+    cnt = np.zeros((nq, 4), np.int64)
+    rc = lib().orc_query(ix.ref(), _p(q), _p(f), _p(aux), nq, k, ls, int(literal), int(s0),
+                         int(scan_cap), _p(ids), _p(dist), _p(cnt), nthreads or default_threads())
+    if rc:
+        raise ValueError("invalid query arguments")
+    return ids, dist, cnt
+
+
+def query_lists(ix: Index, q, filters, aux, ls, nthreads=None):
+    q = _c(q, np.float32)
+    nq = q.shape[0]
+    f = np.ascontiguousarray(filters)
+    aux = _c(aux, np.uint8)
+    ids = np.empty((nq, ls), np.int32)
+    k1 = np.empty((nq, ls), np.uint32)
+    dist = np.empty((nq, ls), np.float32)
+    ln = np.empty(nq, np.int32)
+    lib().orc_query_lists(ix.ref(), _p(q), _p(f), _p(aux), nq, ls, _p(ids), _p(k1), _p(dist),
+                          _p(ln), nthreads or default_threads())
+    return ids, k1, dist, ln
+
+
+def route(ix: Index, filt, aux, s0, scan_cap=32768):
+    f = np.ascontiguousarray(np.atleast_1d(filt))
+    aux = _c(aux, np.uint8)
+    cnt = C.c_int64(0)
+    r = lib().orc_route(ix.ref(), _p(f), _p(aux), int(s0), int(scan_cap), C.byref(cnt))
+    return bool(r), int(cnt.value)
+
+
+def count_passing(ix: Index, filt, aux):
+    f = np.ascontiguousarray(np.atleast_1d(filt))
+    aux = _c(aux, np.uint8)
+    return int(lib().orc_count_passing(ix.ref(), _p(f), _p(aux)))
+
+
+def medoid(x):
+    x = _c(x, np.float32)
+    return int(lib().orc_medoid(_p(x), x.shape[0], x.shape[1]))
+
+
+def sm64(seed, ctr):
+    return int(lib().orc_sm64(seed, ctr))
+
+
+def thresholds(ix: Index, pct=(100, 1, 0), S=500, seed=0, nthreads=None):
+    pct = np.asarray(pct, np.int32)
+    out = np.empty((ix.n, len(pct)), np.uint32)
+    lib().orc_thresholds(ix.ref(), _p(pct), len(pct), S, seed, _p(out), nthreads or default_threads())
+    return out
+
+
+def build(ix: Index, pct=(100, 1, 0), lb=64, alpha=1.2, S=500, seed=0, nthreads=None):
+    """JAG build (Insert + JointRobustPrune over the batch schedule); fills
+    ix.graph and ix.entry, returns the per-point thresholds."""
+    ix.entry = medoid(ix.x)
+    thr = thresholds(ix, pct, S, seed, nthreads)
+    rc = lib().orc_build(ix.ref(), _p(thr), thr.shape[1], int(lb), alpha2_of(alpha),
+                         nthreads or default_threads())
+    if rc:
+        raise RuntimeError("oracle build failed")
+    return thr
+
+
+def joint_prune(ix: Index, p, cand, dpc, T, alpha=1.2):
+    cand = _c(cand, np.int32)
+    dpc = _c(dpc, np.float32)
+    T = _c(T, np.uint32)
+    out = np.empty(ix.R, np.int32)
+    m = lib().orc_joint_prune(ix.ref(), int(p), _p(cand), _p(dpc), len(cand), _p(T), len(T),
+                              alpha2_of(alpha), _p(out))
+    return out[:m]
+
+
+def build_search(ix: Index, p, t, lb, vcap=1 << 16):
+    ids = np.empty(vcap, np.int32)
+    d = np.empty(vcap, np.float32)
+    nv = lib().orc_build_search(ix.ref(), int(p), int(t), int(lb), _p(ids), _p(d), vcap)
+    nv = min(nv, vcap)
+    return ids[:nv], d[:nv]
+
+
+def dist_F(ix: Index, filt, aux, pts):
+    f = np.ascontiguousarray(np.atleast_1d(filt))
+    aux = _c(aux, np.uint8)
+    pts = _c(pts, np.int64)
+    out = np.empty(len(pts), np.uint32)
+    lib().orc_dist_F_batch(ix.ref(), _p(f), _p(aux), _p(pts), len(pts), _p(out))
+    return out
+
+
+def g(ix: Index, filt, aux, pts):
+    f = np.ascontiguousarray(np.atleast_1d(filt))
+    aux = _c(aux, np.uint8)
+    pts = _c(pts, np.int64)
+    out = np.empty(len(pts), np.uint8)
+    lib().orc_g_batch(ix.ref(), _p(f), _p(aux), _p(pts), len(pts), _p(out))
+    return out.astype(bool)
+
+
+def dist_A(ix: Index, i, j):
+    return int(lib().orc_dist_A(ix.ref(), int(i), int(j)))
+
+
+def capped(dist_a, da, t):
+    return int(lib().orc_capped(int(dist_a), int(da), int(t)))
