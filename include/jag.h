@@ -1,0 +1,196 @@
+/*
+ * jag.h -- C ABI of the GB300 filtered nearest-neighbour search library.
+ *
+ * The library implements the query path of JAG (Joint Attribute Graphs,
+ * arXiv 2602.10258): a greedy beam search over a proximity graph in which
+ * candidates are ranked lexicographically by the filter distance dist_F and
+ * then by the squared L2 distance (Sec. 3.2, "Unified comparison rule";
+ * Algorithm 1 "GreedySearch" called with comparator D_F by Algorithm 2
+ * "Query"), for label, range, subset and boolean filters (Sec. 2 "Filter
+ * Constraints", Sec. 3.1 "Examples"); an exact pre-filter scan for the most
+ * selective queries (the Pre-Filtering baseline of the experiments); and the
+ * index build of Algorithms 3 ("Insert") and 4 ("JointRobustPrune") run on
+ * the GPU.
+ *
+ * Conventions shared by every entry point:
+ *   - Plain pointers and sizes only.  "device" pointers are CUDA device
+ *     memory of the index's device; "host" pointers are CPU memory.
+ *   - The caller owns every buffer it passes.  The index owns its own copies
+ *     of vectors, attributes and graph until jag_free().
+ *   - Every call returns a jag_status; JAG_OK is 0.  On failure a message
+ *     for the calling thread is available from jag_last_error().  No call
+ *     aborts, exits or throws across the ABI.
+ *   - Device work is stream-ordered on the stream the caller passes
+ *     (cudaStream_t given as void*, NULL = the legacy default stream).
+ *     Outputs are valid once that stream has reached the call.
+ *   - An index is read-only after jag_build(): concurrent searches on
+ *     different streams are safe.
+ */
+#ifndef JAG_H
+#define JAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define JAG_API __attribute__((visibility("default")))
+#else
+#define JAG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JAG_OK = 0,
+  JAG_EINVAL = 1,       /* bad argument (NULL pointer, size out of range, ...) */
+  JAG_ENOMEM = 2,       /* device memory or scratch budget exhausted           */
+  JAG_ECUDA = 3,        /* a CUDA runtime call failed                           */
+  JAG_ETIMEOUT = 4,     /* a bounded device-side wait gave up                   */
+  JAG_EUNSUPPORTED = 5  /* valid request this build does not handle            */
+} jag_status;
+
+/* Filter kinds (Sec. 2, "Filter Constraints"). */
+typedef enum {
+  JAG_F_NONE = 0,       /* no filter: dist_F = 0 for every point               */
+  JAG_F_LABEL = 1,      /* equality on the int32 attribute                     */
+  JAG_F_RANGE_I32 = 2,  /* lo <= a <= hi on the int32 attribute (inclusive)    */
+  JAG_F_RANGE_F32 = 3,  /* lo <= a <= hi on the float32 attribute (inclusive)  */
+  JAG_F_SUBSET = 4,     /* (f & a) == f on the 64-bit mask attribute           */
+  JAG_F_BOOL = 5        /* f(a) == 1, f a predicate over <= 16 mask bits       */
+} jag_filter_kind;
+
+/* One query filter, 16 bytes.  payload by kind:
+ *   LABEL      low 32 bits: the label (int32)
+ *   RANGE_I32  low 32 bits: lo, high 32 bits: hi (int32, inclusive)
+ *   RANGE_F32  low 32 bits: lo, high 32 bits: hi (float32 bit patterns)
+ *   SUBSET     the required bits
+ *   BOOL       the mask of the involved attribute bits (at most 16 set);
+ *              aux_off is the byte offset in filter_aux of the truth table:
+ *              bit s (little-endian within bytes) is f for the assignment
+ *              whose bit j is the value of the j-th lowest involved bit.
+ * dist_F (Sec. 3.1): label 1[a != f]; range f_min - a below, a - f_max above,
+ * 0 inside; subset popcount(f & ~a); boolean the least number of bit flips
+ * of a that satisfies f (computed exactly from the truth table).  An
+ * unsatisfiable boolean filter matches nothing. */
+typedef struct jag_filter {
+  int32_t kind;
+  int32_t aux_off;
+  uint64_t payload;
+} jag_filter;
+
+/* Element format of the stored base vectors. */
+typedef enum { JAG_VEC_F32 = 0, JAG_VEC_BF16 = 1, JAG_VEC_FP8 = 2 } jag_vec_format;
+
+typedef struct jag_build_params {
+  int64_t n;                    /* number of points, >= 1                      */
+  int64_t d;                    /* dimension, 1..1024                          */
+  const float *x;               /* host [n][d] fp32 base vectors               */
+  const int32_t *attr_i32;      /* host [n] label / integer attribute, or NULL */
+  const float *attr_f32;        /* host [n] float attribute (finite), or NULL  */
+  const uint64_t *attr_mask;    /* host [n] bit-set attribute, or NULL         */
+  int32_t dist_a;               /* attribute the build's dist_A compares:
+                                   JAG_F_LABEL (1[a1 != a2]), JAG_F_RANGE_I32 or
+                                   JAG_F_RANGE_F32 (|a1 - a2|), JAG_F_SUBSET
+                                   (popcount(a1 ^ a2)); Sec. 3.1            */
+  int32_t R;                    /* out-degree bound, 1..64                     */
+  int32_t l_b;                  /* build beam (Algorithm 3), 1..256            */
+  float alpha;                  /* pruning parameter (Algorithm 4), >= 1       */
+  int32_t n_thresholds;         /* |T|, 1..4                                   */
+  int32_t threshold_pct[4];     /* per-point quantiles of dist_A, in percent   */
+  int32_t sample_size;          /* points sampled per threshold estimate (500) */
+  uint64_t seed;                /* seed of the threshold sampling              */
+  int32_t storage;              /* jag_vec_format of the searched vectors      */
+  int32_t device;               /* CUDA device ordinal                         */
+  const int32_t *graph;         /* optional host [n][R] out-lists (-1 padded):
+                                   when given, the build is skipped            */
+  int64_t entry;                /* entry vertex when graph is given            */
+} jag_build_params;
+
+typedef struct jag_index jag_index;   /* opaque */
+
+/* Flags of jag_search_args.flags. */
+#define JAG_SEARCH_SCAN_ALL 0x1  /* answer every query by the exact scan      */
+
+typedef struct jag_search_args {
+  const float *queries;        /* [nq][d] fp32, row-major, unpadded            */
+  const jag_filter *filters;   /* [nq]                                         */
+  const uint8_t *filter_aux;   /* truth tables of boolean filters, or NULL     */
+  int64_t aux_bytes;           /* bytes in filter_aux                          */
+  int64_t nq;                  /* number of queries, >= 0                      */
+  int32_t k;                   /* answers per query, 1..beam                   */
+  int32_t beam;                /* l_s of Algorithm 1, k..256                   */
+  int32_t *out_ids;            /* [nq][k] point ids, -1 padded                 */
+  float *out_dist;             /* [nq][k] squared L2 distances, +inf padded    */
+  void *stream;                /* cudaStream_t, NULL = legacy default stream   */
+  int64_t s0;                  /* route to the exact scan when the estimated
+                                  number of passing points is below s0;
+                                  0 = never, < 0 = default (2048)              */
+  int64_t scan_cap;            /* largest passing set a routed query may have
+                                  (larger ones go back to the graph); <= 0 =
+                                  default (8192)                               */
+  int32_t *counters;           /* optional [nq][4] int32: hops, first-seen
+                                  neighbours, distance computations, routed    */
+  int32_t flags;               /* JAG_SEARCH_* bits                            */
+  int32_t hash_bits;           /* log2 slots of the visited set, 0 = default   */
+  void *ev_graph_begin;        /* optional cudaEvent_t recorded just before
+                                  the graph-search kernel                      */
+  void *ev_graph_end;          /* ... and just after it                        */
+} jag_search_args;
+
+/* Build an index on a device (Algorithms 3-4 run on the GPU; Sec. 3.3 and the
+ * implementation-details appendix), or upload a given graph.  Host inputs
+ * are copied; the call returns when the index is ready.  Errors: JAG_EINVAL
+ * for bad sizes, NULL vectors, a missing attribute column for dist_a,
+ * non-finite vectors or float attributes; JAG_ENOMEM; JAG_ECUDA. */
+JAG_API jag_status jag_build(const jag_build_params *params, jag_index **out);
+
+/* Query (Algorithm 2) for nq queries: device pointers, asynchronous on
+ * args->stream.  Queries whose estimated passing count is below s0 are
+ * answered by the exact scan, the others by GreedySearch with D_F.  Each
+ * answer list holds the best k points with dist_F = 0 among the final
+ * candidate list, sorted by (distance, id), padded with -1 / +inf.  Uses a
+ * library-owned scratch buffer per stream (allocated on first use).
+ * Errors: JAG_EINVAL (NULL pointers, k/beam out of range, d mismatch),
+ * JAG_ENOMEM, JAG_ECUDA. */
+JAG_API jag_status jag_search(jag_index *idx, const jag_search_args *args);
+
+/* Same as jag_search with HOST buffers for queries, filters, aux and
+ * outputs: copies them to and from the device inside the call and returns
+ * when the answers are in host memory.  args->stream may be NULL. */
+JAG_API jag_status jag_search_host(jag_index *idx, const jag_search_args *args);
+
+/* Index facts. */
+typedef struct jag_info {
+  int64_t n, d;
+  int32_t R, storage;
+  int64_t entry;
+  int64_t device_bytes;         /* bytes the index holds on the device         */
+  double build_seconds;         /* wall time of the GPU build, 0 if uploaded   */
+  int32_t n_thresholds, dist_a;
+} jag_info;
+JAG_API jag_status jag_get_info(const jag_index *idx, jag_info *out);
+
+/* Copy the out-lists [n][R] (-1 padded) to host memory. */
+JAG_API jag_status jag_get_graph(const jag_index *idx, int32_t *host_out);
+
+/* Copy the per-point thresholds [n][n_thresholds] (dist_A in the ordered
+ * 32-bit form: integer value, or float bit pattern) to host memory;
+ * JAG_EINVAL if the graph was uploaded rather than built. */
+JAG_API jag_status jag_get_thresholds(const jag_index *idx, uint32_t *host_out);
+
+/* Release the index and its device memory.  NULL is allowed. */
+JAG_API void jag_free(jag_index *idx);
+
+/* Message of the calling thread's last failed call ("" if none). */
+JAG_API const char *jag_last_error(void);
+
+/* Library version string. */
+JAG_API const char *jag_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JAG_H */

@@ -88,8 +88,10 @@ def _c(a, dtype):
 
 
 def alpha2_of(alpha: float) -> float:
-    """fp32 value of alpha^2, computed in double and rounded once."""
-    return float(np.float32(float(alpha) * float(alpha)))
+    """alpha^2 as the pruning test uses it: alpha is an fp32 parameter, its
+    square is formed in double and rounded once to fp32."""
+    a = float(np.float32(alpha))
+    return float(np.float32(a * a))
 
 
 class Index:

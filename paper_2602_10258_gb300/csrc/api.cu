@@ -1,0 +1,444 @@
+// C ABI of the library (include/jag.h): argument checks, device memory of an
+// index, per-stream scratch, and the launch sequences of search and build.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "jag.h"
+#include "launch.h"
+#include "search_core.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+jag_status fail(jag_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+jag_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? JAG_ENOMEM : JAG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Buffer {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Device scratch owned by the library, one per stream.
+struct Workspace {
+  std::mutex mu;
+  Buffer buf;
+};
+
+// Device staging for jag_search_host.
+struct HostStage {
+  std::mutex mu;
+  Buffer q, f, aux, ids, dist, cnt;
+  cudaStream_t stream = nullptr;
+};
+
+cudaError_t ensure(Buffer &b, size_t bytes, cudaStream_t stream) {
+  if (b.bytes >= bytes && b.ptr) return cudaSuccess;
+  if (b.ptr) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = std::max<size_t>(bytes, 4096);
+  cudaError_t e = cudaMalloc(&b.ptr, want);
+  if (e != cudaSuccess) { b.ptr = nullptr; return e; }
+  b.bytes = want;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+struct jag_index {
+  int device = 0;
+  jag::DevIndex ix{};
+  int64_t n = 0, d = 0;
+  int32_t R = 0, storage = JAG_VEC_F32, nT = 0, dist_a = 0;
+  std::vector<void *> allocs;
+  size_t device_bytes = 0;
+  double build_seconds = 0.0;
+  float *x = nullptr;
+  int32_t *graph = nullptr;
+  uint32_t *thr = nullptr;
+  std::mutex mu;
+  std::unordered_map<cudaStream_t, Workspace *> ws;
+  HostStage host;
+
+  ~jag_index() {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    for (auto &kv : ws) {
+      if (kv.second->buf.ptr) cudaFree(kv.second->buf.ptr);
+      delete kv.second;
+    }
+    for (Buffer *b : {&host.q, &host.f, &host.aux, &host.ids, &host.dist, &host.cnt})
+      if (b->ptr) cudaFree(b->ptr);
+    if (host.stream) cudaStreamDestroy(host.stream);
+    for (void *p : allocs) cudaFree(p);
+    cudaSetDevice(prev);
+  }
+
+  cudaError_t alloc(void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 256);
+    if (e == cudaSuccess) { allocs.push_back(*p); device_bytes += bytes; }
+    return e;
+  }
+
+  Workspace *workspace(cudaStream_t s) {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = ws.find(s);
+    if (it != ws.end()) return it->second;
+    Workspace *w = new Workspace();
+    ws.emplace(s, w);
+    return w;
+  }
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = 0;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+template <class T>
+bool all_finite(const T *v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite((double)v[i])) return false;
+  return true;
+}
+
+template <class V>
+void sorted_column(const V *vals, int64_t n, std::vector<V> &sv, std::vector<int32_t> &si) {
+  std::vector<std::pair<V, int32_t>> tmp((size_t)n);
+  for (int64_t i = 0; i < n; ++i) tmp[(size_t)i] = {vals[i], (int32_t)i};
+  std::sort(tmp.begin(), tmp.end());
+  sv.resize((size_t)n);
+  si.resize((size_t)n);
+  for (int64_t i = 0; i < n; ++i) { sv[(size_t)i] = tmp[(size_t)i].first; si[(size_t)i] = tmp[(size_t)i].second; }
+}
+
+int default_hash_bits(int ls) { return ls <= 64 ? 11 : (ls <= 128 ? 12 : 13); }
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
+  if (!idx) return fail(JAG_EINVAL, "index is NULL");
+  if (!a) return fail(JAG_EINVAL, "args is NULL");
+  if (a->nq < 0) return fail(JAG_EINVAL, "nq < 0");
+  if (a->nq > 0 && (!a->queries || !a->filters || !a->out_ids || !a->out_dist))
+    return fail(JAG_EINVAL, "NULL query, filter or output pointer");
+  if (a->beam < 1 || a->beam > 256) return fail(JAG_EINVAL, "beam must be in [1, 256]");
+  if (a->k < 1 || a->k > a->beam) return fail(JAG_EINVAL, "k must be in [1, beam]");
+  if (a->aux_bytes < 0 || (a->aux_bytes > 0 && !a->filter_aux)) return fail(JAG_EINVAL, "bad filter_aux");
+  if (a->nq > (int64_t)1 << 31) return fail(JAG_EINVAL, "nq too large");
+  int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
+  if (hb < 5 || hb > 16) return fail(JAG_EINVAL, "hash_bits must be in [5, 16]");
+  const int cap = jag::list_capacity(a->beam);
+  if ((size_t)jag::kSearchWarps * jag::warp_smem_bytes(cap, hb) > kSmemLimit)
+    return fail(JAG_EINVAL, "hash_bits too large for the beam");
+  return JAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *jag_last_error(void) { return g_err.c_str(); }
+
+const char *jag_version(void) { return "jag-gb300 0.1 (sm_103a)"; }
+
+jag_status jag_build(const jag_build_params *p, jag_index **out) {
+  g_err.clear();
+  if (!p || !out) return fail(JAG_EINVAL, "NULL params or out");
+  *out = nullptr;
+  if (p->n < 1 || p->n >= ((int64_t)1 << 31) - 1) return fail(JAG_EINVAL, "n out of range");
+  if (p->d < 1 || p->d > 1024) return fail(JAG_EINVAL, "d must be in [1, 1024]");
+  if (!p->x) return fail(JAG_EINVAL, "x is NULL");
+  if (p->R < 1 || p->R > 64) return fail(JAG_EINVAL, "R must be in [1, 64]");
+  if (p->storage != JAG_VEC_F32) return fail(JAG_EUNSUPPORTED, "storage format not available in this build");
+  const bool prebuilt = p->graph != nullptr;
+  if (!prebuilt) {
+    if (p->l_b < 1 || p->l_b > 256) return fail(JAG_EINVAL, "l_b must be in [1, 256]");
+    if (!(p->alpha >= 1.0f) || !std::isfinite(p->alpha)) return fail(JAG_EINVAL, "alpha must be finite and >= 1");
+    if (p->n_thresholds < 1 || p->n_thresholds > 4) return fail(JAG_EINVAL, "n_thresholds must be in [1, 4]");
+    for (int i = 0; i < p->n_thresholds; ++i)
+      if (p->threshold_pct[i] < 0 || p->threshold_pct[i] > 100) return fail(JAG_EINVAL, "threshold_pct out of [0,100]");
+    if (p->sample_size < 1 || p->sample_size > 1024) return fail(JAG_EINVAL, "sample_size must be in [1, 1024]");
+    switch (p->dist_a) {
+      case JAG_F_LABEL: case JAG_F_RANGE_I32:
+        if (!p->attr_i32) return fail(JAG_EINVAL, "dist_a needs attr_i32");
+        break;
+      case JAG_F_RANGE_F32:
+        if (!p->attr_f32) return fail(JAG_EINVAL, "dist_a needs attr_f32");
+        break;
+      case JAG_F_SUBSET: case JAG_F_BOOL:
+        if (!p->attr_mask) return fail(JAG_EINVAL, "dist_a needs attr_mask");
+        break;
+      default: return fail(JAG_EINVAL, "bad dist_a");
+    }
+  } else if (p->entry < 0 || p->entry >= p->n) {
+    return fail(JAG_EINVAL, "entry out of range");
+  }
+  const int64_t n = p->n, d = p->d;
+  if (!all_finite(p->x, (size_t)(n * d))) return fail(JAG_EINVAL, "non-finite base vector element");
+  if (p->attr_f32 && !all_finite(p->attr_f32, (size_t)n)) return fail(JAG_EINVAL, "non-finite float attribute");
+  if (prebuilt) {
+    for (int64_t i = 0; i < n * p->R; ++i)
+      if (p->graph[i] < -1 || p->graph[i] >= n) return fail(JAG_EINVAL, "graph id out of range");
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return fail(JAG_ECUDA, "no CUDA device");
+  if (p->device < 0 || p->device >= ndev) return fail(JAG_EINVAL, "device ordinal out of range");
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return fail(JAG_ECUDA, "cudaSetDevice failed");
+
+  auto *I = new jag_index();
+  I->device = p->device;
+  I->n = n; I->d = d; I->R = p->R; I->storage = p->storage;
+  I->dist_a = p->dist_a;
+  cudaError_t e;
+  const int64_t xs = (d + 3) / 4 * 4;
+  jag::DevIndex &ix = I->ix;
+  ix.n = n; ix.d = (int32_t)d; ix.xs = xs; ix.nchunks = (int32_t)(xs / 4); ix.R = p->R; ix.dist_a = p->dist_a;
+  auto bail = [&](jag_status s) { delete I; return s; };
+#define API_TRY(x, what) do { e = (x); if (e != cudaSuccess) { jag_status s_ = cuda_fail(e, what); return bail(s_); } } while (0)
+  API_TRY(I->alloc((void **)&I->x, sizeof(float) * (size_t)(n * xs)), "allocate vectors");
+  API_TRY(cudaMemset(I->x, 0, sizeof(float) * (size_t)(n * xs)), "clear vectors");
+  API_TRY(cudaMemcpy2D(I->x, sizeof(float) * xs, p->x, sizeof(float) * d, sizeof(float) * d, (size_t)n,
+                       cudaMemcpyHostToDevice), "copy vectors");
+  ix.x = I->x;
+  if (p->attr_i32) {
+    int32_t *a, *sv, *si;
+    API_TRY(I->alloc((void **)&a, 4 * (size_t)n), "allocate attr_i32");
+    API_TRY(cudaMemcpy(a, p->attr_i32, 4 * (size_t)n, cudaMemcpyHostToDevice), "copy attr_i32");
+    std::vector<int32_t> v, id;
+    sorted_column(p->attr_i32, n, v, id);
+    API_TRY(I->alloc((void **)&sv, 4 * (size_t)n), "allocate sorted column");
+    API_TRY(I->alloc((void **)&si, 4 * (size_t)n), "allocate sorted column");
+    API_TRY(cudaMemcpy(sv, v.data(), 4 * (size_t)n, cudaMemcpyHostToDevice), "copy sorted column");
+    API_TRY(cudaMemcpy(si, id.data(), 4 * (size_t)n, cudaMemcpyHostToDevice), "copy sorted column");
+    ix.a_i32 = a; ix.si32_val = sv; ix.si32_id = si;
+  }
+  if (p->attr_f32) {
+    float *a, *sv;
+    int32_t *si;
+    API_TRY(I->alloc((void **)&a, 4 * (size_t)n), "allocate attr_f32");
+    API_TRY(cudaMemcpy(a, p->attr_f32, 4 * (size_t)n, cudaMemcpyHostToDevice), "copy attr_f32");
+    std::vector<float> v;
+    std::vector<int32_t> id;
+    sorted_column(p->attr_f32, n, v, id);
+    API_TRY(I->alloc((void **)&sv, 4 * (size_t)n), "allocate sorted column");
+    API_TRY(I->alloc((void **)&si, 4 * (size_t)n), "allocate sorted column");
+    API_TRY(cudaMemcpy(sv, v.data(), 4 * (size_t)n, cudaMemcpyHostToDevice), "copy sorted column");
+    API_TRY(cudaMemcpy(si, id.data(), 4 * (size_t)n, cudaMemcpyHostToDevice), "copy sorted column");
+    ix.a_f32 = a; ix.sf32_val = sv; ix.sf32_id = si;
+  }
+  if (p->attr_mask) {
+    uint64_t *a;
+    API_TRY(I->alloc((void **)&a, 8 * (size_t)n), "allocate attr_mask");
+    API_TRY(cudaMemcpy(a, p->attr_mask, 8 * (size_t)n, cudaMemcpyHostToDevice), "copy attr_mask");
+    ix.a_mask = a;
+  }
+  API_TRY(I->alloc((void **)&I->graph, sizeof(int32_t) * (size_t)(n * p->R)), "allocate graph");
+  ix.graph = I->graph;
+  if (prebuilt) {
+    API_TRY(cudaMemcpy(I->graph, p->graph, sizeof(int32_t) * (size_t)(n * p->R), cudaMemcpyHostToDevice),
+            "copy graph");
+    ix.entry = (int32_t)p->entry;
+  } else {
+    I->nT = p->n_thresholds;
+    API_TRY(I->alloc((void **)&I->thr, sizeof(uint32_t) * (size_t)(n * I->nT)), "allocate thresholds");
+    jag::BuildLaunch B{};
+    B.ix = ix;
+    B.graph = I->graph;
+    B.thr = I->thr;
+    B.nT = I->nT;
+    for (int i = 0; i < 4; ++i) B.pct[i] = i < I->nT ? p->threshold_pct[i] : 0;
+    B.sample = p->sample_size;
+    B.seed = p->seed;
+    B.lb = p->l_b;
+    B.alpha2 = (float)((double)p->alpha * (double)p->alpha);
+    cudaStream_t st;
+    API_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "create stream");
+    B.stream = st;
+    char msg[256] = {0};
+    int32_t entry = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = jag::run_build(B, &entry, msg, sizeof(msg));
+    auto t1 = std::chrono::steady_clock::now();
+    cudaStreamDestroy(st);
+    if (rc != JAG_OK) { jag_status s_ = fail((jag_status)rc, "%s", msg); return bail(s_); }
+    ix.entry = entry;
+    I->build_seconds = std::chrono::duration<double>(t1 - t0).count();
+  }
+  API_TRY(cudaDeviceSynchronize(), "finish upload");
+#undef API_TRY
+  *out = I;
+  return JAG_OK;
+}
+
+void jag_free(jag_index *idx) { delete idx; }
+
+jag_status jag_get_info(const jag_index *idx, jag_info *out) {
+  if (!idx || !out) return fail(JAG_EINVAL, "NULL argument");
+  out->n = idx->n; out->d = idx->d; out->R = idx->R; out->storage = idx->storage;
+  out->entry = idx->ix.entry; out->device_bytes = (int64_t)idx->device_bytes;
+  out->build_seconds = idx->build_seconds; out->n_thresholds = idx->nT; out->dist_a = idx->dist_a;
+  return JAG_OK;
+}
+
+jag_status jag_get_graph(const jag_index *idx, int32_t *host_out) {
+  if (!idx || !host_out) return fail(JAG_EINVAL, "NULL argument");
+  DeviceGuard dg(idx->device);
+  cudaError_t e = cudaMemcpy(host_out, idx->graph, sizeof(int32_t) * (size_t)(idx->n * idx->R), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? JAG_OK : cuda_fail(e, "copy graph");
+}
+
+jag_status jag_get_thresholds(const jag_index *idx, uint32_t *host_out) {
+  if (!idx || !host_out) return fail(JAG_EINVAL, "NULL argument");
+  if (!idx->thr) return fail(JAG_EINVAL, "index graph was uploaded, not built");
+  DeviceGuard dg(idx->device);
+  cudaError_t e = cudaMemcpy(host_out, idx->thr, sizeof(uint32_t) * (size_t)(idx->n * idx->nT), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? JAG_OK : cuda_fail(e, "copy thresholds");
+}
+
+static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream_t stream) {
+  const int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
+  const int64_t s0 = a->s0 < 0 ? 2048 : a->s0;
+  const int64_t cap = a->scan_cap <= 0 ? 8192 : a->scan_cap;
+  const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
+  int32_t ntiles;
+  int64_t tile;
+  const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, cap, a->k, idx->n, scan_all, &ntiles, &tile);
+  Workspace *w = idx->workspace(stream);
+  std::lock_guard<std::mutex> g(w->mu);
+  cudaError_t e = ensure(w->buf, L0.total, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "allocate search scratch");
+  uint8_t *base = (uint8_t *)w->buf.ptr;
+  jag::SearchLaunch L{};
+  L.ix = idx->ix;
+  L.queries = a->queries;
+  L.d = (int32_t)idx->d;
+  L.filters = a->filters;
+  L.aux = a->filter_aux;
+  L.aux_bytes = a->aux_bytes;
+  L.nq = a->nq;
+  L.k = a->k; L.ls = a->beam; L.hbits = hb;
+  L.s0 = s0; L.cap = cap; L.scan_all = scan_all;
+  L.out_ids = a->out_ids; L.out_dist = a->out_dist; L.counters = a->counters;
+  L.plans = (jag::QueryPlan *)(base + L0.plans);
+  L.lut = base + L0.lut;
+  L.lists = (int32_t *)(base + L0.lists);
+  L.list_counts = (int32_t *)(base + L0.list_counts);
+  L.work = (unsigned long long *)(base + L0.work);
+  L.status = (uint32_t *)(base + L0.status);
+  L.part_key = (uint64_t *)(base + L0.part_key);
+  L.part_id = (uint32_t *)(base + L0.part_id);
+  L.ntiles = ntiles; L.tile = tile;
+  L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
+  L.ev_end = (cudaEvent_t)a->ev_graph_end;
+  L.stream = stream;
+  e = cudaMemsetAsync(L.status, 0, 4, stream);
+  if (e == cudaSuccess) e = jag::run_search(L);
+  if (e != cudaSuccess) return cuda_fail(e, "search launch");
+  return JAG_OK;
+}
+
+jag_status jag_search(jag_index *idx, const jag_search_args *a) {
+  g_err.clear();
+  jag_status s = check_search_args(idx, a);
+  if (s != JAG_OK) return s;
+  DeviceGuard dg(idx->device);
+  if (!dg.ok) return fail(JAG_ECUDA, "cudaSetDevice failed");
+  return search_on(idx, a, (cudaStream_t)a->stream);
+}
+
+jag_status jag_search_host(jag_index *idx, const jag_search_args *a) {
+  g_err.clear();
+  jag_status s = check_search_args(idx, a);
+  if (s != JAG_OK) return s;
+  DeviceGuard dg(idx->device);
+  if (!dg.ok) return fail(JAG_ECUDA, "cudaSetDevice failed");
+  HostStage &H = idx->host;
+  std::lock_guard<std::mutex> g(H.mu);
+  cudaError_t e = cudaSuccess;
+  cudaStream_t st = (cudaStream_t)a->stream;
+  if (!st) {
+    if (!H.stream && (e = cudaStreamCreateWithFlags(&H.stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "create stream");
+    st = H.stream;
+  }
+  const size_t qb = sizeof(float) * (size_t)(a->nq * idx->d), fb = sizeof(jag_filter) * (size_t)a->nq;
+  const size_t ob = sizeof(int32_t) * (size_t)(a->nq * a->k), db = sizeof(float) * (size_t)(a->nq * a->k);
+  const size_t cb = a->counters ? sizeof(int32_t) * 4 * (size_t)a->nq : 0;
+  if ((e = ensure(H.q, qb, st)) || (e = ensure(H.f, fb, st)) || (e = ensure(H.aux, (size_t)a->aux_bytes, st)) ||
+      (e = ensure(H.ids, ob, st)) || (e = ensure(H.dist, db, st)) || (e = ensure(H.cnt, cb, st)))
+    return cuda_fail(e, "allocate staging");
+  if (a->nq > 0) {
+    if ((e = cudaMemcpyAsync(H.q.ptr, a->queries, qb, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(H.f.ptr, a->filters, fb, cudaMemcpyHostToDevice, st)))
+      return cuda_fail(e, "copy inputs");
+  }
+  if (a->aux_bytes > 0 && (e = cudaMemcpyAsync(H.aux.ptr, a->filter_aux, (size_t)a->aux_bytes, cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e, "copy filter aux");
+  jag_search_args d = *a;
+  d.queries = (const float *)H.q.ptr;
+  d.filters = (const jag_filter *)H.f.ptr;
+  d.filter_aux = a->aux_bytes > 0 ? (const uint8_t *)H.aux.ptr : nullptr;
+  d.out_ids = (int32_t *)H.ids.ptr;
+  d.out_dist = (float *)H.dist.ptr;
+  d.counters = a->counters ? (int32_t *)H.cnt.ptr : nullptr;
+  d.stream = st;
+  s = search_on(idx, &d, st);
+  if (s != JAG_OK) return s;
+  if (a->nq > 0) {
+    if ((e = cudaMemcpyAsync(a->out_ids, H.ids.ptr, ob, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(a->out_dist, H.dist.ptr, db, cudaMemcpyDeviceToHost, st)))
+      return cuda_fail(e, "copy outputs");
+    if (cb && (e = cudaMemcpyAsync(a->counters, H.cnt.ptr, cb, cudaMemcpyDeviceToHost, st)))
+      return cuda_fail(e, "copy counters");
+  }
+  uint32_t status = 0;
+  Workspace *w = idx->workspace(st);
+  if (w->buf.ptr) {
+    int32_t ntiles;
+    int64_t tile;
+    const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, a->scan_cap <= 0 ? 8192 : a->scan_cap,
+                                                             a->k, idx->n, (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0,
+                                                             &ntiles, &tile);
+    if ((e = cudaMemcpyAsync(&status, (uint8_t *)w->buf.ptr + L0.status, 4, cudaMemcpyDeviceToHost, st)))
+      return cuda_fail(e, "read status");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "search");
+  if (status & jag::kErrBadFilter) return fail(JAG_EINVAL, "invalid filter record(s): their answers are padded");
+  return JAG_OK;
+}
+
+}  // extern "C"

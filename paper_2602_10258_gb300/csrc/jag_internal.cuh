@@ -1,0 +1,205 @@
+// Internal device-side definitions of the JAG search library (sm_103a).
+//
+// Data layout in device memory (one index):
+//   x        fp32 rows, stride xs floats (d rounded up to a multiple of 4,
+//            zero padded) so that every row starts on a 16-byte boundary and
+//            is read as 16-byte chunks;
+//   graph    int32 [n][R] out-lists, -1 padded (one 128-byte row at R = 32);
+//   a_i32 / a_f32 / a_mask   per-point attribute columns (structure of arrays);
+//   s*_val / s*_id           the int32 / float32 column sorted by (value, id):
+//            label and range filters read their passing set as one slice.
+//
+// Ordered keys.  Candidates are compared lexicographically by
+// (first component, squared distance, id) (Sec. 3.2, "Unified comparison
+// rule"; the id is a final tie-break).  The first component is dist_F for a
+// query and the capped dist_A for the build, kept as a 32-bit unsigned: an
+// integer distance, or the bit pattern of a non-negative float, which orders
+// like the value.  (first, distance bits) form one 64-bit key.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jag.h"
+
+namespace jag {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kExpanded = 0x80000000u;   // beam id flag: vertex expanded
+constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;  // visited-set empty slot
+constexpr uint64_t kNoKey = ~0ull;
+
+enum Route : int32_t { kRouteGraph = 0, kRouteSlice = 1, kRouteList = 2, kRouteSkip = 3 };
+
+struct DevIndex {
+  int64_t n;
+  int32_t d;
+  int32_t nchunks;      // 16-byte chunks per stored fp32 row = xs / 4
+  int64_t xs;           // row stride in floats
+  const float *x;
+  const int32_t *graph;
+  int32_t R;
+  int32_t entry;
+  int32_t dist_a;
+  int32_t pad0;
+  const int32_t *a_i32;
+  const float *a_f32;
+  const uint64_t *a_mask;
+  const int32_t *si32_val;
+  const int32_t *si32_id;
+  const float *sf32_val;
+  const int32_t *sf32_id;
+};
+
+// Per-query plan written by the preparation kernel.
+struct QueryPlan {
+  int32_t route;        // Route
+  int32_t lut_off;      // byte offset of the boolean distance table, -1 if none
+  int64_t begin, end;   // passing slice of a sorted column (kRouteSlice)
+  int32_t count;        // passing points gathered for kRouteList
+  int32_t est;          // estimated / exact passing count used by the router
+};
+
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t f2u(float f) { return __float_as_uint(f); }
+__device__ __forceinline__ float u2f(uint32_t u) { return __uint_as_float(u); }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ int32_t lo32(uint64_t p) { return (int32_t)(uint32_t)(p & 0xFFFFFFFFu); }
+__device__ __forceinline__ int32_t hi32(uint64_t p) { return (int32_t)(uint32_t)(p >> 32); }
+
+// Compress the bits of a selected by vars into the low bits, lowest first.
+__device__ __forceinline__ uint32_t compress_bits(uint64_t a, uint64_t vars) {
+  uint32_t s = 0;
+  int j = 0;
+  while (vars) {
+    int pos = __ffsll((long long)vars) - 1;
+    s |= (uint32_t)((a >> pos) & 1ull) << j;
+    ++j;
+    vars &= vars - 1;
+  }
+  return s;
+}
+
+// g(a, f) of Sec. 2 for point u.  tt: the boolean filter's truth table.
+__device__ __forceinline__ bool passes(const DevIndex &ix, int64_t u, int32_t kind, uint64_t pay,
+                                       const uint8_t *tt) {
+  switch (kind) {
+    case JAG_F_NONE: return true;
+    case JAG_F_LABEL: return ix.a_i32[u] == lo32(pay);
+    case JAG_F_RANGE_I32: {
+      int32_t a = ix.a_i32[u];
+      return lo32(pay) <= a && a <= hi32(pay);
+    }
+    case JAG_F_RANGE_F32: {
+      float a = ix.a_f32[u];
+      return u2f((uint32_t)lo32(pay)) <= a && a <= u2f((uint32_t)hi32(pay));
+    }
+    case JAG_F_SUBSET: return (pay & ix.a_mask[u]) == pay;
+    case JAG_F_BOOL: {
+      uint32_t s = compress_bits(ix.a_mask[u], pay);
+      return (tt[s >> 3] >> (s & 7)) & 1;
+    }
+    default: return false;
+  }
+}
+
+// dist_F(a_u, f) in ordered 32-bit form (Sec. 3.1, "Examples").  lut: the
+// per-query boolean table (least flips per assignment of involved bits).
+__device__ __forceinline__ uint32_t filter_distance(const DevIndex &ix, int64_t u, int32_t kind,
+                                                    uint64_t pay, const uint8_t *lut) {
+  switch (kind) {
+    case JAG_F_NONE: return 0u;
+    case JAG_F_LABEL: return ix.a_i32[u] != lo32(pay) ? 1u : 0u;
+    case JAG_F_RANGE_I32: {
+      int64_t a = ix.a_i32[u], lo = lo32(pay), hi = hi32(pay);
+      if (a < lo) return (uint32_t)(lo - a);
+      if (a > hi) return (uint32_t)(a - hi);
+      return 0u;
+    }
+    case JAG_F_RANGE_F32: {
+      float a = ix.a_f32[u];
+      float lo = u2f((uint32_t)lo32(pay)), hi = u2f((uint32_t)hi32(pay));
+      if (a < lo) return f2u(__fsub_rn(lo, a));
+      if (a > hi) return f2u(__fsub_rn(a, hi));
+      if (lo <= a && a <= hi) return 0u;
+      return 0x7F800000u;  // NaN bound: never satisfied
+    }
+    case JAG_F_SUBSET: return (uint32_t)__popcll(pay & ~ix.a_mask[u]);
+    case JAG_F_BOOL: return lut[compress_bits(ix.a_mask[u], pay)];
+    default: return 0x7F800000u;
+  }
+}
+
+// dist_A(a_i, a_j) in ordered form (Sec. 3.1) for the build's attribute.
+__device__ __forceinline__ uint32_t attribute_distance(const DevIndex &ix, int64_t i, int64_t j) {
+  switch (ix.dist_a) {
+    case JAG_F_LABEL: return ix.a_i32[i] != ix.a_i32[j] ? 1u : 0u;
+    case JAG_F_RANGE_I32: {
+      int64_t t = (int64_t)ix.a_i32[i] - (int64_t)ix.a_i32[j];
+      return (uint32_t)(t < 0 ? -t : t);
+    }
+    case JAG_F_RANGE_F32: return f2u(fabsf(__fsub_rn(ix.a_f32[i], ix.a_f32[j])));
+    default: return (uint32_t)__popcll(ix.a_mask[i] ^ ix.a_mask[j]);
+  }
+}
+
+// dist_A(.,.; t) = max(dist_A - t, 0) (Sec. 3.2, "Capped attribute distance").
+__device__ __forceinline__ uint32_t capped_distance(int32_t dist_a, uint32_t da, uint32_t t) {
+  if (dist_a == JAG_F_RANGE_F32) {
+    float fa = u2f(da), ft = u2f(t);
+    return fa > ft ? f2u(__fsub_rn(fa, ft)) : 0u;
+  }
+  return da > t ? da - t : 0u;
+}
+
+__device__ __forceinline__ bool key_less(uint64_t ak, uint32_t aid, uint64_t bk, uint32_t bid) {
+  return ak < bk || (ak == bk && aid < bid);
+}
+
+__device__ __forceinline__ uint64_t make_key(uint32_t first, float dist) {
+  return ((uint64_t)first << 32) | (uint64_t)f2u(dist);
+}
+
+// 16-byte read-only gather of one chunk of a stored row.
+__device__ __forceinline__ float4 ld_chunk(const float *p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// acc <- fma(t, t, acc) over the four elements of one chunk, in order, with
+// t = q - x rounded to fp32.  Element order and rounding are part of the
+// distance's definition; no contraction beyond these explicit fmas.
+__device__ __forceinline__ float chunk_accumulate(float acc, float4 q, float4 x) {
+  float t;
+  t = __fsub_rn(q.x, x.x); acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(q.y, x.y); acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(q.z, x.z); acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(q.w, x.w); acc = __fmaf_rn(t, t, acc);
+  return acc;
+}
+
+// Butterfly over the P lanes of a group: acc_l + acc_(l xor o), o = P/2..1.
+template <int P>
+__device__ __forceinline__ float group_reduce(float acc) {
+#pragma unroll
+  for (int o = P / 2; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(kFull, acc, o));
+  return acc;
+}
+
+// Status word bits written by kernels (read back by the host where needed).
+enum : uint32_t {
+  kErrVisitedOverflow = 1u,
+  kErrCandOverflow = 2u,
+  kErrBadFilter = 4u,
+};
+
+}  // namespace jag

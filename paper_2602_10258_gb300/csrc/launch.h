@@ -1,0 +1,71 @@
+// Host-side launch interface between the C ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jag_internal.cuh"
+
+namespace jag {
+
+// One jag_search call, resolved to device pointers.
+struct SearchLaunch {
+  DevIndex ix;
+  const float *queries;
+  int32_t d;
+  const jag_filter *filters;
+  const uint8_t *aux;
+  int64_t aux_bytes;
+  int64_t nq;
+  int32_t k, ls, hbits;
+  int64_t s0, cap;
+  int32_t scan_all;
+  int32_t *out_ids;
+  float *out_dist;
+  int32_t *counters;
+  // scratch
+  QueryPlan *plans;
+  uint8_t *lut;
+  int32_t *lists;          // [nq][cap] passing ids of list-routed queries
+  int32_t *list_counts;    // [nq]
+  unsigned long long *work;  // [4] work counters
+  uint32_t *status;
+  uint64_t *part_key;      // brute-force partial lists [nq][ntiles][k]
+  uint32_t *part_id;
+  int32_t ntiles;
+  int64_t tile;
+  cudaEvent_t ev_begin, ev_end;
+  cudaStream_t stream;
+};
+
+// Scratch layout of a search; sizes in bytes, offsets 256-aligned.
+struct SearchScratch {
+  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, total;
+};
+SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int64_t n,
+                                    int scan_all, int32_t *ntiles, int64_t *tile);
+
+cudaError_t run_search(const SearchLaunch &L);
+
+// Smallest supported list capacity >= ls (64, 128 or 256); 0 if ls > 256.
+int list_capacity(int ls);
+// Lanes per row P and chunks per lane for a row of nchunks 16-byte chunks.
+bool row_mapping(int nchunks, int *P, int *CPL);
+
+// GPU index build (Algorithms 3 and 4); see build.cu.
+struct BuildLaunch {
+  DevIndex ix;              // graph pointer is writable
+  int32_t *graph;
+  uint32_t *thr;            // [n][nT]
+  int32_t nT;
+  int32_t pct[4];
+  int32_t sample;
+  uint64_t seed;
+  int32_t lb;
+  float alpha2;
+  cudaStream_t stream;
+};
+// Returns 0 on success, else a jag_status code; msg receives a description.
+int run_build(BuildLaunch &B, int32_t *entry_out, char *msg, size_t msg_len);
+
+}  // namespace jag

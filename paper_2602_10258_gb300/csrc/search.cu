@@ -1,0 +1,547 @@
+// Query path kernels: filter preparation and routing, attribute gather for
+// routed subset/boolean filters, the query kernel (graph search or exact scan
+// per query) and the brute-force scan.
+#include <algorithm>
+#include <mutex>
+
+#include "launch.h"
+#include "search_core.cuh"
+
+namespace jag {
+
+constexpr int kPrepWarps = 8;
+constexpr int kGatherTile = 4096;
+constexpr int kGatherQPB = 64;   // queries per gather CTA
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *v, int64_t n, int32_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) { int64_t m = (lo + hi) >> 1; if (v[m] < x) lo = m + 1; else hi = m; }
+  return lo;
+}
+__device__ __forceinline__ int64_t upper_bound_i32(const int32_t *v, int64_t n, int32_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) { int64_t m = (lo + hi) >> 1; if (v[m] <= x) lo = m + 1; else hi = m; }
+  return lo;
+}
+__device__ __forceinline__ int64_t lower_bound_f32(const float *v, int64_t n, float x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) { int64_t m = (lo + hi) >> 1; if (v[m] < x) lo = m + 1; else hi = m; }
+  return lo;
+}
+__device__ __forceinline__ int64_t upper_bound_f32(const float *v, int64_t n, float x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) { int64_t m = (lo + hi) >> 1; if (v[m] <= x) lo = m + 1; else hi = m; }
+  return lo;
+}
+
+// Boolean distance table of one filter (Sec. 3.1, boolean example):
+// lut[s] = least Hamming distance from assignment s of the m involved bits to
+// an assignment where the truth table is 1 (255 if there is none).  Computed
+// one dimension at a time: the Hamming metric is a sum over bits, so relaxing
+// each pair (s, s ^ 2^j) once per bit j gives the exact distances.
+__device__ void build_bool_lut(const uint8_t *tt, int m, uint8_t *lut) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t S = 1u << m;
+  for (uint32_t s = lane; s < S; s += 32) lut[s] = ((tt[s >> 3] >> (s & 7)) & 1) ? 0 : 255;
+  __syncwarp();
+  for (int j = 0; j < m; ++j) {
+    const uint32_t low = (1u << j) - 1;
+    for (uint32_t i = lane; i < (S >> 1); i += 32) {
+      const uint32_t s = ((i & ~low) << 1) | (i & low);
+      const uint32_t t = s | (1u << j);
+      const int a = lut[s], b = lut[t];
+      lut[s] = (uint8_t)min(a, b + 1);
+      lut[t] = (uint8_t)min(b, a + 1);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ void pad_outputs(int64_t qi, int k, int32_t *out_ids, float *out_dist) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < k; j += 32) {
+    out_ids[qi * k + j] = -1;
+    out_dist[qi * k + j] = __int_as_float(0x7F800000);
+  }
+}
+
+// K0: validate each filter, build boolean tables, and route the query:
+// label/range filters count their passing set exactly (binary search in the
+// sorted column); subset/boolean filters are estimated on the fixed sample of
+// S = min(4096, n) points with ids floor(j n / S).  A query whose count
+// (estimate) is below s0 goes to the exact scan.
+__global__ void __launch_bounds__(kPrepWarps * 32)
+prep_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, int64_t aux_bytes, int64_t nq,
+            int64_t s0, int64_t cap, int scan_all, QueryPlan *plans, uint8_t *lut_base, int32_t *list_counts, int k,
+            int32_t *out_ids, float *out_dist, int32_t *counters, uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * kPrepWarps;
+  for (int64_t qi = (int64_t)blockIdx.x * kPrepWarps + (threadIdx.x >> 5); qi < nq; qi += wstride) {
+    const jag_filter f = filters[qi];
+    QueryPlan pl;
+    pl.route = kRouteGraph; pl.lut_off = -1; pl.begin = 0; pl.end = 0; pl.count = 0; pl.est = 0;
+    bool ok;
+    int m = 0;
+    switch (f.kind) {
+      case JAG_F_NONE: ok = true; break;
+      case JAG_F_LABEL: case JAG_F_RANGE_I32: ok = ix.a_i32 != nullptr; break;
+      case JAG_F_RANGE_F32: ok = ix.a_f32 != nullptr; break;
+      case JAG_F_SUBSET: ok = ix.a_mask != nullptr; break;
+      case JAG_F_BOOL: {
+        m = __popcll(f.payload);
+        const int64_t tbytes = ((int64_t)1 << m) / 8 > 0 ? ((int64_t)1 << m) / 8 : 1;
+        ok = ix.a_mask != nullptr && aux != nullptr && m <= 16 && f.aux_off >= 0 &&
+             (int64_t)f.aux_off + tbytes <= aux_bytes;
+        break;
+      }
+      default: ok = false;
+    }
+    if (!ok) {
+      pl.route = kRouteSkip;
+      if (lane == 0) {
+        plans[qi] = pl;
+        atomicOr(status, kErrBadFilter);
+        if (counters) { counters[qi * 4 + 0] = 0; counters[qi * 4 + 1] = 0; counters[qi * 4 + 2] = 0; counters[qi * 4 + 3] = 0; }
+      }
+      pad_outputs(qi, k, out_ids, out_dist);
+      continue;
+    }
+    const uint8_t *tt = nullptr;
+    if (f.kind == JAG_F_BOOL) {
+      tt = aux + f.aux_off;
+      pl.lut_off = f.aux_off * 8;
+      build_bool_lut(tt, m, lut_base + pl.lut_off);
+    }
+    if (scan_all) {
+      pl.route = kRouteSkip + 1;   // brute-force scan
+    } else if (s0 > 0) {
+      if (f.kind == JAG_F_LABEL || f.kind == JAG_F_RANGE_I32 || f.kind == JAG_F_RANGE_F32) {
+        int64_t b = 0, e = 0;
+        if (lane == 0) {
+          if (f.kind == JAG_F_LABEL) {
+            b = lower_bound_i32(ix.si32_val, ix.n, lo32(f.payload));
+            e = upper_bound_i32(ix.si32_val, ix.n, lo32(f.payload));
+          } else if (f.kind == JAG_F_RANGE_I32) {
+            const int32_t lo = lo32(f.payload), hi = hi32(f.payload);
+            if (lo <= hi) { b = lower_bound_i32(ix.si32_val, ix.n, lo); e = upper_bound_i32(ix.si32_val, ix.n, hi); }
+          } else {
+            const float lo = u2f((uint32_t)lo32(f.payload)), hi = u2f((uint32_t)hi32(f.payload));
+            if (lo <= hi) { b = lower_bound_f32(ix.sf32_val, ix.n, lo); e = upper_bound_f32(ix.sf32_val, ix.n, hi); }
+          }
+        }
+        b = __shfl_sync(kFull, b, 0);
+        e = __shfl_sync(kFull, e, 0);
+        pl.begin = b; pl.end = e;
+        pl.est = (int32_t)min64(e - b, 0x7FFFFFFF);
+        if (e - b < s0 && e - b <= cap) pl.route = kRouteSlice;
+      } else if (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) {
+        const int64_t S = ix.n < 4096 ? ix.n : 4096;
+        int hits = 0;
+        for (int64_t j = lane; j < S; j += 32) hits += passes(ix, j * ix.n / S, f.kind, f.payload, tt) ? 1 : 0;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) hits += __shfl_xor_sync(kFull, hits, o);
+        pl.est = hits;
+        if ((int64_t)hits * ix.n < s0 * S) {
+          pl.route = kRouteList;
+          if (lane == 0) list_counts[qi] = 0;
+        }
+      }
+    }
+    if (lane == 0) plans[qi] = pl;
+  }
+}
+
+// K2: one pass over a tile of masks evaluates the predicates of up to
+// kGatherQPB list-routed queries and appends the passing ids.
+__global__ void __launch_bounds__(256)
+gather_list_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, const QueryPlan *plans,
+                   int64_t nq, int64_t cap, int32_t *lists, int32_t *counts) {
+  __shared__ uint64_t sm[kGatherTile];
+  const int64_t t0 = (int64_t)blockIdx.x * kGatherTile;
+  const int64_t t1 = min64(ix.n, t0 + kGatherTile);
+  const int64_t q0 = (int64_t)blockIdx.y * kGatherQPB;
+  // skip the tile load when no query of this group is list-routed
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  if (threadIdx.x < kGatherQPB && q0 + threadIdx.x < nq && plans[q0 + threadIdx.x].route == kRouteList) any = 1;
+  __syncthreads();
+  if (!any) return;
+  for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) sm[i - t0] = ix.a_mask[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int qq = warp; qq < kGatherQPB; qq += nw) {
+    const int64_t qi = q0 + qq;
+    if (qi >= nq) break;
+    if (plans[qi].route != kRouteList) continue;
+    const jag_filter f = filters[qi];
+    const uint8_t *tt = f.kind == JAG_F_BOOL ? aux + f.aux_off : nullptr;
+    for (int64_t b = t0; b < t1; b += 32) {
+      const int64_t u = b + lane;
+      bool pass = false;
+      if (u < t1) {
+        const uint64_t a = sm[u - t0];
+        if (f.kind == JAG_F_SUBSET) pass = (f.payload & a) == f.payload;
+        else { const uint32_t s = compress_bits(a, f.payload); pass = (tt[s >> 3] >> (s & 7)) & 1; }
+      }
+      const uint32_t m = __ballot_sync(kFull, pass);
+      if (!m) continue;
+      int off = 0;
+      if (lane == 0) off = atomicAdd(&counts[qi], __popc(m));
+      off = __shfl_sync(kFull, off, 0);
+      if (pass) {
+        const int64_t pos = off + __popc(m & lanemask_lt());
+        if (pos < cap) lists[qi * cap + pos] = (int32_t)u;
+      }
+    }
+  }
+}
+
+// A list-routed query whose passing set exceeds the scan capacity goes back
+// to the graph search.
+__global__ void finalize_routes_kernel(QueryPlan *plans, const int32_t *counts, int64_t nq, int64_t cap) {
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= nq) return;
+  if (plans[qi].route != kRouteList) return;
+  const int32_t c = counts[qi];
+  plans[qi].count = c;
+  if (c > cap) plans[qi].route = kRouteGraph;
+}
+
+__device__ __forceinline__ void write_answers(const WarpSmem &S, int cnt, int64_t qi, int k, int32_t *out_ids,
+                                              float *out_dist) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < k; j += 32) {
+    int32_t id = -1;
+    float dd = __int_as_float(0x7F800000);
+    if (j < cnt) {
+      const uint64_t kk = S.bkey[j];
+      if ((kk >> 32) == 0) { id = (int32_t)(S.bid[j] & ~kExpanded); dd = u2f((uint32_t)kk); }
+    }
+    out_ids[qi * k + j] = id;
+    out_dist[qi * k + j] = dd;
+  }
+}
+
+// Exact top-k over an explicit candidate id list (all candidates pass the
+// filter), kept in the warp's list with the same merge as the search.
+template <int CAP, int P, int CPL>
+__device__ int scan_candidates(const DevIndex &ix, const float4 (&q)[CPL], const int32_t *ids, int64_t m, int k,
+                               const WarpSmem &S) {
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  for (int64_t b = 0; b < m; b += 32) {
+    const int nc = (int)min64(32, m - b);
+    if (lane < nc) S.cid[lane] = (uint32_t)ids[b + lane];
+    __syncwarp();
+    const bool full = cnt == k;
+    const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
+    const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
+    const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+    uint64_t ck = kNoKey;
+    uint32_t cv = kEmptySlot;
+    if (lane < nc) {
+      ck = make_key(0u, dist);
+      cv = S.cid[lane];
+      if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+    }
+    warp_sort32(ck, cv);
+    __syncwarp();
+    int r0;
+    cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, k, ck, cv, r0);
+  }
+  return cnt;
+}
+
+// K1/K3: each warp takes queries from a global counter; a graph-routed query
+// runs GreedySearch with D_F (Algorithm 2), a scan-routed one the exact scan
+// over its passing slice or list.
+template <int CAP, int P, int CPL>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
+             const uint8_t *lut_base, const int32_t *lists, int64_t cap, int64_t nq, int k, int ls, int hbits,
+             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(CAP, hbits), CAP, hbits);
+  for (;;) {
+    unsigned long long qi = 0;
+    if (lane == 0) qi = atomicAdd(work, 1ull);
+    qi = __shfl_sync(kFull, qi, 0);
+    if (qi >= (unsigned long long)nq) return;
+    const QueryPlan pl = plans[qi];
+    if (pl.route == kRouteSkip || pl.route > kRouteSkip) continue;
+    float4 q[CPL];
+    load_point<P, CPL>(queries + (int64_t)qi * d, d, q);
+    if (pl.route == kRouteGraph) {
+      const jag_filter f = filters[qi];
+      const QueryKey key{f.kind, f.payload, pl.lut_off >= 0 ? lut_base + pl.lut_off : nullptr};
+      NoSink sink;
+      SearchStats st;
+      const int cnt = greedy_search<CAP, P, CPL>(ix, key, q, ls, hbits, S, sink, st);
+      write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
+      if (counters && lane == 0) {
+        int32_t *c = counters + qi * 4;
+        c[0] = st.hops; c[1] = st.seen; c[2] = st.dcs; c[3] = 0;
+      }
+    } else {
+      const int32_t *ids;
+      int64_t m;
+      if (pl.route == kRouteSlice) {
+        const int32_t kind = filters[qi].kind;
+        ids = (kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
+        m = pl.end - pl.begin;
+      } else {
+        ids = lists + (int64_t)qi * cap;
+        m = pl.count;
+      }
+      const int cnt = scan_candidates<CAP, P, CPL>(ix, q, ids, m, k, S);
+      write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
+      if (counters && lane == 0) {
+        int32_t *c = counters + qi * 4;
+        c[0] = 0; c[1] = 0; c[2] = (int32_t)m; c[3] = 1;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Brute force: every point of a tile is tested against the filter and the
+// passing ones ranked exactly; partial lists are merged per query afterwards.
+template <int CAP, int P, int CPL>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const uint8_t *aux,
+                  const QueryPlan *plans, int64_t nq, int k, int64_t tile, int ntiles, uint64_t *part_key,
+                  uint32_t *part_id) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(CAP, 5), CAP, 5);
+  const int64_t qi = (int64_t)blockIdx.y * kSearchWarps + warp;
+  if (qi >= nq) return;
+  const int t = blockIdx.x;
+  uint64_t *pk = part_key + (qi * ntiles + t) * k;
+  uint32_t *pi = part_id + (qi * ntiles + t) * k;
+  if (plans[qi].route != kRouteSkip + 1) {
+    for (int j = lane; j < k; j += 32) { pk[j] = kNoKey; pi[j] = kEmptySlot; }
+    return;
+  }
+  const jag_filter f = filters[qi];
+  const uint8_t *tt = f.kind == JAG_F_BOOL ? aux + f.aux_off : nullptr;
+  float4 q[CPL];
+  load_point<P, CPL>(queries + qi * d, d, q);
+  const int64_t b0 = (int64_t)t * tile, b1 = min64(ix.n, b0 + tile);
+  int cnt = 0;
+  for (int64_t b = b0; b < b1; b += 32) {
+    const int64_t u = b + lane;
+    const bool pass = u < b1 && passes(ix, u, f.kind, f.payload, tt);
+    const uint32_t pm = __ballot_sync(kFull, pass);
+    if (!pm) continue;
+    const int nc = __popc(pm);
+    if (pass) S.cid[__popc(pm & lanemask_lt())] = (uint32_t)u;
+    __syncwarp();
+    const bool full = cnt == k;
+    const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
+    const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
+    const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+    uint64_t ck = kNoKey;
+    uint32_t cv = kEmptySlot;
+    if (lane < nc) {
+      ck = make_key(0u, dist);
+      cv = S.cid[lane];
+      if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+    }
+    warp_sort32(ck, cv);
+    __syncwarp();
+    int r0;
+    cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, k, ck, cv, r0);
+  }
+  for (int j = lane; j < k; j += 32) {
+    pk[j] = j < cnt ? S.bkey[j] : kNoKey;
+    pi[j] = j < cnt ? S.bid[j] : kEmptySlot;
+  }
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const uint64_t *part_key,
+                   const uint32_t *part_id, int32_t *out_ids, float *out_dist, int32_t *counters) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(CAP, 5), CAP, 5);
+  const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + warp;
+  if (qi >= nq) return;
+  if (plans[qi].route != kRouteSkip + 1) return;   // padded by the preparation kernel
+  int cnt = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    for (int b = 0; b < k; b += 32) {
+      uint64_t ck = kNoKey;
+      uint32_t cv = kEmptySlot;
+      if (b + lane < k) {
+        ck = part_key[(qi * ntiles + t) * k + b + lane];
+        cv = part_id[(qi * ntiles + t) * k + b + lane];
+      }
+      if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
+      warp_sort32(ck, cv);
+      __syncwarp();
+      int r0;
+      cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, k, ck, cv, r0);
+    }
+  }
+  write_answers(S, cnt, qi, k, out_ids, out_dist);
+  if (counters && lane == 0) {
+    int32_t *c = counters + qi * 4;
+    c[0] = 0; c[1] = 0; c[2] = 0; c[3] = 2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+int list_capacity(int ls) {
+  if (ls <= 64) return 64;
+  if (ls <= 128) return 128;
+  if (ls <= 256) return 256;
+  return 0;
+}
+
+bool row_mapping(int nchunks, int *P, int *CPL) {
+  if (nchunks <= 8) { *P = 8; *CPL = 1; }
+  else if (nchunks <= 16) { *P = 16; *CPL = 1; }
+  else if (nchunks <= 32) { *P = 32; *CPL = 1; }
+  else if (nchunks <= 64) { *P = 32; *CPL = 2; }
+  else if (nchunks <= 128) { *P = 32; *CPL = 4; }
+  else if (nchunks <= 256) { *P = 32; *CPL = 8; }
+  else return false;
+  return true;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int64_t n,
+                                    int scan_all, int32_t *ntiles, int64_t *tile) {
+  SearchScratch s;
+  size_t off = 0;
+  s.plans = off; off += align256(sizeof(QueryPlan) * (size_t)std::max<int64_t>(nq, 1));
+  s.lut = off; off += align256((size_t)std::max<int64_t>(aux_bytes, 1) * 8);
+  s.lists = off; off += scan_all ? 256 : align256((size_t)std::max<int64_t>(nq, 1) * (size_t)cap * 4);
+  s.list_counts = off; off += align256((size_t)std::max<int64_t>(nq, 1) * 4);
+  s.work = off; off += 256;
+  s.status = off; off += 256;
+  int64_t t = 65536;
+  int32_t nt = (int32_t)((n + t - 1) / t);
+  if (nt < 1) nt = 1;
+  *ntiles = nt;
+  *tile = t;
+  const size_t parts = scan_all ? (size_t)std::max<int64_t>(nq, 1) * nt * k : 1;
+  s.part_key = off; off += align256(parts * 8);
+  s.part_id = off; off += align256(parts * 4);
+  s.total = off;
+  return s;
+}
+
+template <class Kern>
+static int blocks_per_sm(Kern kern, size_t smem) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kSearchWarps * 32, smem) != cudaSuccess) b = 1;
+  return b > 0 ? b : 0;
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int CAP, int P, int CPL>
+static cudaError_t launch_query(const SearchLaunch &L) {
+  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(CAP, L.hbits);
+  auto kern = query_kernel<CAP, P, CPL>;
+  const int bps = blocks_per_sm(kern, smem);
+  if (bps == 0) return cudaErrorInvalidConfiguration;
+  int64_t want = (L.nq + kSearchWarps - 1) / kSearchWarps;
+  int64_t grid = std::min<int64_t>((int64_t)bps * num_sms(), std::max<int64_t>(want, 1));
+  if (L.ev_begin) cudaEventRecord(L.ev_begin, L.stream);
+  kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(
+      L.ix, L.queries, L.d, L.filters, L.plans, L.lut, L.lists, L.cap, L.nq, L.k, L.ls, L.hbits, L.out_ids,
+      L.out_dist, L.counters, L.work);
+  if (L.ev_end) cudaEventRecord(L.ev_end, L.stream);
+  return cudaGetLastError();
+}
+
+template <int CAP, int P, int CPL>
+static cudaError_t launch_brute(const SearchLaunch &L) {
+  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(CAP, 5);
+  auto kern = brute_tile_kernel<CAP, P, CPL>;
+  if (blocks_per_sm(kern, smem) == 0) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)L.ntiles, (unsigned)((L.nq + kSearchWarps - 1) / kSearchWarps));
+  kern<<<grid, kSearchWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.aux, L.plans, L.nq, L.k,
+                                                     L.tile, L.ntiles, L.part_key, L.part_id);
+  auto mk = merge_parts_kernel<CAP>;
+  if (blocks_per_sm(mk, smem) == 0) return cudaErrorInvalidConfiguration;
+  mk<<<(unsigned)((L.nq + kSearchWarps - 1) / kSearchWarps), kSearchWarps * 32, smem, L.stream>>>(
+      L.plans, L.nq, L.k, L.ntiles, L.part_key, L.part_id, L.out_ids, L.out_dist, L.counters);
+  return cudaGetLastError();
+}
+
+template <int CAP>
+static cudaError_t dispatch_rows(const SearchLaunch &L, int P, int CPL, bool brute) {
+#define JAG_CASE(PP, CC)                                                          \
+  if (P == PP && CPL == CC) return brute ? launch_brute<CAP, PP, CC>(L) : launch_query<CAP, PP, CC>(L);
+  JAG_CASE(8, 1)
+  JAG_CASE(16, 1)
+  JAG_CASE(32, 1)
+  JAG_CASE(32, 2)
+  JAG_CASE(32, 4)
+  JAG_CASE(32, 8)
+#undef JAG_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t run_search(const SearchLaunch &L) {
+  if (L.nq == 0) return cudaSuccess;
+  int P, CPL;
+  if (!row_mapping(L.ix.nchunks, &P, &CPL)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(L.work, 0, 256, L.stream)) != cudaSuccess) return e;
+  {
+    int64_t blocks = std::min<int64_t>((L.nq + kPrepWarps - 1) / kPrepWarps, (int64_t)num_sms() * 16);
+    prep_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, L.stream>>>(
+        L.ix, L.filters, L.aux, L.aux_bytes, L.nq, L.s0, L.cap, L.scan_all, L.plans, L.lut, L.list_counts, L.k,
+        L.out_ids, L.out_dist, L.counters, L.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (L.scan_all) {
+    const int cap = list_capacity(L.k);
+    switch (cap) {
+      case 64: return dispatch_rows<64>(L, P, CPL, true);
+      case 128: return dispatch_rows<128>(L, P, CPL, true);
+      case 256: return dispatch_rows<256>(L, P, CPL, true);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (L.s0 > 0 && L.ix.a_mask) {
+    dim3 grid((unsigned)((L.ix.n + kGatherTile - 1) / kGatherTile), (unsigned)((L.nq + kGatherQPB - 1) / kGatherQPB));
+    gather_list_kernel<<<grid, 256, 0, L.stream>>>(L.ix, L.filters, L.aux, L.plans, L.nq, L.cap, L.lists,
+                                                   L.list_counts);
+    finalize_routes_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.plans, L.list_counts, L.nq,
+                                                                                 L.cap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  switch (list_capacity(L.ls)) {
+    case 64: return dispatch_rows<64>(L, P, CPL, false);
+    case 128: return dispatch_rows<128>(L, P, CPL, false);
+    case 256: return dispatch_rows<256>(L, P, CPL, false);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace jag

@@ -1,0 +1,338 @@
+// GreedySearch (Algorithm 1 of the paper) executed by one warp.
+//
+// One warp owns one search.  Its candidate list L (at most l_s entries,
+// sorted by (first key, distance, id)) and a hashed visited set live in the
+// warp's slice of shared memory; nothing else is kept per search.  Each hop:
+//   select   the first unexpanded entry p of L (ballot over 32 entries);
+//   fetch    p's out-list: one coalesced 4-byte load per lane (128 B at R=32);
+//   dedupe   each lane tests/inserts its neighbour in the visited set
+//            (shared-memory open addressing on full ids, atomicCAS);
+//   filter   first key (dist_F or capped dist_A) from the neighbour's
+//            attribute; a key above a full list's last entry is dropped
+//            without touching its vector (exact: that entry's key only
+//            decreases, so the neighbour could never be kept);
+//   gather   survivors' rows as 16-byte chunks, P lanes per row, 32/P rows
+//            per warp-wide load, several loads in flight;
+//   reduce   squared L2 in the fixed order: chunk g -> lane g mod 32,
+//            elements of a chunk in order by fma, then the butterfly
+//            acc_l + acc_(l xor o) for o = 16..1 (groups of P < 32 lanes only
+//            skip steps that would add exact zeros);
+//   merge    warp bitonic sort of the <= 32 new keys, then an in-place merge
+//            into L that keeps the best l_s and drops a neighbour already in
+//            L (equal key and id);
+// until every entry of L is expanded.
+//
+// The visited set may forget (it is cleared when three quarters full): that
+// only costs recomputation, because an id still in L is caught by the merge
+// (same key, same id) and an id that left L can never re-enter it.
+#pragma once
+
+#include "jag_internal.cuh"
+
+namespace jag {
+
+constexpr int kSearchWarps = 4;   // warps (searches) per CTA
+
+// Shared-memory slice of one warp.
+struct WarpSmem {
+  uint64_t *bkey;   // [cap] keys of L
+  uint32_t *bid;    // [cap] ids of L, bit 31 = expanded
+  uint32_t *hash;   // [1 << hbits] visited set
+  uint32_t *cid;    // [32] candidate ids of the current hop
+  uint32_t *ck1;    // [32] their first keys
+  uint32_t *rank;   // [32] merge ranks
+};
+
+__host__ __device__ inline size_t warp_smem_bytes(int cap, int hbits) {
+  return (size_t)cap * 12 + ((size_t)4 << hbits) + 32 * 4 * 3;
+}
+
+__device__ inline WarpSmem carve_warp_smem(uint8_t *base, int cap, int hbits) {
+  WarpSmem s;
+  s.bkey = reinterpret_cast<uint64_t *>(base);
+  s.bid = reinterpret_cast<uint32_t *>(base + (size_t)cap * 8);
+  s.hash = reinterpret_cast<uint32_t *>(base + (size_t)cap * 12);
+  s.cid = s.hash + (1u << hbits);
+  s.ck1 = s.cid + 32;
+  s.rank = s.ck1 + 32;
+  return s;
+}
+
+// Ascending bitonic sort of one (key, id) pair per lane.
+__device__ __forceinline__ void warp_sort32(uint64_t &key, uint32_t &id) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint64_t ok = __shfl_xor_sync(kFull, key, j);
+      uint32_t oi = __shfl_xor_sync(kFull, id, j);
+      bool up = (lane & k) == 0;
+      bool lower = (lane & j) == 0;
+      bool other_less = key_less(ok, oi, key, id);
+      bool take = (lower == up) ? other_less : !other_less;
+      if (take) { key = ok; id = oi; }
+    }
+  }
+}
+
+__device__ __forceinline__ int first_unexpanded(const uint32_t *bid, int cnt, int start) {
+  const int lane = threadIdx.x & 31;
+  for (int b = start; b < cnt; b += 32) {
+    int j = b + lane;
+    bool un = (j < cnt) && !(bid[j] & kExpanded);
+    uint32_t m = __ballot_sync(kFull, un);
+    if (m) return b + __ffs(m) - 1;
+  }
+  return -1;
+}
+
+// Visited-set probe; returns true if id was not recorded (new or forgotten).
+__device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t id, bool &inserted) {
+  const uint32_t mask = (1u << hbits) - 1;
+  const uint32_t h = (id * 0x9E3779B1u) >> (32 - hbits);
+  inserted = false;
+#pragma unroll 1
+  for (int probe = 0; probe < 8; ++probe) {
+    uint32_t slot = (h + probe) & mask;
+    uint32_t old = atomicCAS(&tab[slot], kEmptySlot, id);
+    if (old == kEmptySlot) { inserted = true; return true; }
+    if (old == id) return false;
+  }
+  return true;
+}
+
+// Merge the lane-held sorted candidates (invalid = kNoKey) into L[0..cnt):
+// keep the best ls, drop candidates already present.  Returns the new count;
+// r0 receives the smallest insertion position (cnt if none).
+template <int CAP>
+__device__ __forceinline__ int merge_into_list(uint64_t *bkey, uint32_t *bid, uint32_t *s_rank, int cnt,
+                                               int ls, uint64_t ck, uint32_t cidv, int &r0) {
+  const int lane = threadIdx.x & 31;
+  bool valid = ck != kNoKey;
+  int rank = 0;
+  if (valid) {
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (key_less(bkey[mid], bid[mid] & ~kExpanded, ck, cidv)) lo = mid + 1;
+      else hi = mid;
+    }
+    rank = lo;
+    if (rank >= ls) valid = false;
+    else if (rank < cnt && bkey[rank] == ck && (bid[rank] & ~kExpanded) == cidv) valid = false;
+  }
+  const uint32_t vm = __ballot_sync(kFull, valid);
+  r0 = cnt;
+  if (vm == 0) return cnt;
+  const int nv = __popc(vm);
+  const int vi = __popc(vm & lanemask_lt());
+  if (valid) s_rank[vi] = (uint32_t)rank;
+  r0 = __shfl_sync(kFull, rank, __ffs(vm) - 1);
+  constexpr int PER = CAP / 32;
+  uint64_t ek[PER];
+  uint32_t ei[PER];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    int j = r0 + lane + 32 * t;
+    if (j < cnt) { ek[t] = bkey[j]; ei[t] = bid[j]; }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    int j = r0 + lane + 32 * t;
+    if (j < cnt) {
+      int lo = 0, hi = nv;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((int)s_rank[mid] <= j) lo = mid + 1;
+        else hi = mid;
+      }
+      int np = j + lo;
+      if (np < ls) { bkey[np] = ek[t]; bid[np] = ei[t]; }
+    }
+  }
+  if (valid) {
+    int np = vi + rank;
+    if (np < ls) { bkey[np] = ck; bid[np] = cidv; }
+  }
+  __syncwarp();
+  int n2 = cnt + nv;
+  return n2 < ls ? n2 : ls;
+}
+
+// Distances from the search point (lane-held chunks q) to the nc rows whose
+// ids are cid[0..nc); lane c < nc returns the distance of candidate c.
+template <int P, int CPL>
+__device__ __forceinline__ float candidate_distances(const DevIndex &ix, const float4 (&q)[CPL],
+                                                     const uint32_t *cid, int nc) {
+  constexpr int VPW = 32 / P;                 // rows per warp-wide load
+  constexpr int U = (VPW * 8 <= 32) ? 8 / VPW : 1;   // loads in flight per lane
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / P, lig = lane % P;
+  float mine = 0.f;
+  for (int base = 0; base < nc; base += VPW * U) {
+    float4 xv[U][CPL];
+#pragma unroll
+    for (int s = 0; s < U; ++s) {
+      const int c = base + s * VPW + grp;
+      const bool ok = c < nc;
+      const float *row = ix.x + (int64_t)(ok ? cid[c] : 0u) * ix.xs;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int ch = lig + j * 32;
+        xv[s][j] = (ok && ch < ix.nchunks) ? ld_chunk(row + ch * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < U; ++s) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) acc = chunk_accumulate(acc, q[j], xv[s][j]);
+      acc = group_reduce<P>(acc);
+      const int c0 = base + s * VPW;
+      const float v = __shfl_sync(kFull, acc, ((lane - c0) * P) & 31);
+      if (lane >= c0 && lane < c0 + VPW) mine = v;
+    }
+  }
+  return mine;
+}
+
+// Lane chunks of a search point given as a contiguous fp32 row of d values
+// (not necessarily 16-byte aligned); elements past d are zero.
+template <int P, int CPL>
+__device__ __forceinline__ void load_point(const float *row, int d, float4 (&q)[CPL]) {
+  const int lig = (threadIdx.x & 31) % P;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int e = (lig + j * 32) * 4;
+    q[j].x = e + 0 < d ? row[e + 0] : 0.f;
+    q[j].y = e + 1 < d ? row[e + 1] : 0.f;
+    q[j].z = e + 2 < d ? row[e + 2] : 0.f;
+    q[j].w = e + 3 < d ? row[e + 3] : 0.f;
+  }
+}
+
+// First-key policies.
+struct QueryKey {   // dist_F of the query's filter (Sec. 3.1)
+  int32_t kind;
+  uint64_t payload;
+  const uint8_t *lut;
+  __device__ __forceinline__ uint32_t operator()(const DevIndex &ix, int64_t u) const {
+    return filter_distance(ix, u, kind, payload, lut);
+  }
+};
+
+struct BuildKey {   // capped dist_A from base point p with threshold t (Sec. 3.2)
+  int64_t p;
+  uint32_t t;
+  __device__ __forceinline__ uint32_t operator()(const DevIndex &ix, int64_t u) const {
+    return capped_distance(ix.dist_a, attribute_distance(ix, p, u), t);
+  }
+};
+
+struct NoSink {
+  __device__ __forceinline__ void visit(int, uint32_t, uint64_t) {}
+};
+
+// Records the expanded vertices (the set V of Algorithm 1) with their
+// distances from the search point.
+struct VisitSink {
+  uint32_t *ids;
+  float *dist;
+  int cap;
+  int n;
+  __device__ __forceinline__ void visit(int lane, uint32_t id, uint64_t key) {
+    if (lane == 0 && n < cap) { ids[n] = id; dist[n] = u2f((uint32_t)key); }
+    ++n;
+  }
+};
+
+struct SearchStats {
+  int hops, seen, dcs;
+};
+
+// Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
+// hold the final list L (count returned).
+template <int CAP, int P, int CPL, class KeyFn, class Sink>
+__device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4 (&q)[CPL], int ls,
+                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t hsize = 1u << hbits;
+  for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
+  __syncwarp();
+  uint32_t fill = 1;
+  const int32_t s = ix.entry;
+  if (lane == 0) { S.cid[0] = (uint32_t)s; S.hash[((uint32_t)s * 0x9E3779B1u) >> (32 - hbits)] = (uint32_t)s; }
+  __syncwarp();
+  {
+    const float d0 = candidate_distances<P, CPL>(ix, q, S.cid, 1);
+    const uint32_t k0 = key1(ix, s);
+    const float d0b = __shfl_sync(kFull, d0, 0);
+    if (lane == 0) { S.bkey[0] = make_key(k0, d0b); S.bid[0] = (uint32_t)s; }
+  }
+  __syncwarp();
+  int cnt = 1, start = 0;
+  st.hops = 0; st.seen = 0; st.dcs = 1;
+  for (;;) {
+    const int sel = first_unexpanded(S.bid, cnt, start);
+    if (sel < 0) break;
+    const uint32_t pid = S.bid[sel];
+    const uint64_t pkey = S.bkey[sel];
+    __syncwarp();
+    if (lane == 0) S.bid[sel] = pid | kExpanded;
+    sink.visit(lane, pid, pkey);
+    st.hops += 1;
+    const int32_t *row = ix.graph + (int64_t)pid * ix.R;
+    int rmin = cnt;
+    for (int rb = 0; rb < ix.R; rb += 32) {
+      const int u = (rb + lane < ix.R) ? __ldg(row + rb + lane) : -1;
+      bool inserted = false, fresh = false;
+      if (u >= 0) fresh = visit_insert(S.hash, hbits, (uint32_t)u, inserted);
+      fill += __popc(__ballot_sync(kFull, inserted));
+      st.seen += __popc(__ballot_sync(kFull, fresh));
+      const bool full = (cnt == ls);
+      const uint64_t tkey = full ? S.bkey[ls - 1] : kNoKey;
+      const uint32_t tid = full ? (S.bid[ls - 1] & ~kExpanded) : kEmptySlot;
+      uint32_t k1 = 0;
+      bool keep = fresh;
+      if (fresh) {
+        k1 = key1(ix, u);
+        keep = !(full && k1 > (uint32_t)(tkey >> 32));
+      }
+      const uint32_t km = __ballot_sync(kFull, keep);
+      const int nc = __popc(km);
+      if (keep) {
+        const int r = __popc(km & lanemask_lt());
+        S.cid[r] = (uint32_t)u;
+        S.ck1[r] = k1;
+      }
+      __syncwarp();
+      if (nc == 0) continue;
+      st.dcs += nc;
+      const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+      uint64_t ck = kNoKey;
+      uint32_t cv = kEmptySlot;
+      if (lane < nc) {
+        ck = make_key(S.ck1[lane], dist);
+        cv = S.cid[lane];
+        if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+      }
+      warp_sort32(ck, cv);
+      __syncwarp();
+      int r0;
+      cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, ls, ck, cv, r0);
+      rmin = r0 < rmin ? r0 : rmin;
+    }
+    start = (sel + 1) < rmin ? (sel + 1) : rmin;
+    if (fill > (hsize >> 1) + (hsize >> 2)) {
+      __syncwarp();
+      for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
+      fill = 0;
+      __syncwarp();
+    }
+  }
+  return cnt;
+}
+
+}  // namespace jag

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of the C ABI in ``include/jag.h``.
+
+Argument marshalling only: every step of index build and search runs in the
+CUDA library ``libjag.so``.  Device buffers and streams come from PyTorch
+(``torch.Tensor.data_ptr()``, ``torch.cuda.Stream.cuda_stream``).  If the
+library cannot be loaded, every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build_ext
+from .datagen import FILTER_DTYPE
+
+JAG_OK, JAG_EINVAL, JAG_ENOMEM, JAG_ECUDA, JAG_ETIMEOUT, JAG_EUNSUPPORTED = range(6)
+JAG_F_NONE, JAG_F_LABEL, JAG_F_RANGE_I32, JAG_F_RANGE_F32, JAG_F_SUBSET, JAG_F_BOOL = range(6)
+JAG_VEC_F32, JAG_VEC_BF16, JAG_VEC_FP8 = range(3)
+JAG_SEARCH_SCAN_ALL = 0x1
+
+_STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+
+
+class JagError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("jag status %s (%d): %s" % (_STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("x", C.c_void_p), ("attr_i32", C.c_void_p),
+                ("attr_f32", C.c_void_p), ("attr_mask", C.c_void_p), ("dist_a", C.c_int32),
+                ("R", C.c_int32), ("l_b", C.c_int32), ("alpha", C.c_float),
+                ("n_thresholds", C.c_int32), ("threshold_pct", C.c_int32 * 4),
+                ("sample_size", C.c_int32), ("seed", C.c_uint64), ("storage", C.c_int32),
+                ("device", C.c_int32), ("graph", C.c_void_p), ("entry", C.c_int64)]
+
+
+class SearchArgs(C.Structure):
+    _fields_ = [("queries", C.c_void_p), ("filters", C.c_void_p), ("filter_aux", C.c_void_p),
+                ("aux_bytes", C.c_int64), ("nq", C.c_int64), ("k", C.c_int32), ("beam", C.c_int32),
+                ("out_ids", C.c_void_p), ("out_dist", C.c_void_p), ("stream", C.c_void_p),
+                ("s0", C.c_int64), ("scan_cap", C.c_int64), ("counters", C.c_void_p),
+                ("flags", C.c_int32), ("hash_bits", C.c_int32), ("ev_graph_begin", C.c_void_p),
+                ("ev_graph_end", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("R", C.c_int32), ("storage", C.c_int32),
+                ("entry", C.c_int64), ("device_bytes", C.c_int64), ("build_seconds", C.c_double),
+                ("n_thresholds", C.c_int32), ("dist_a", C.c_int32)]
+
+
+EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_get_info", "jag_get_graph",
+            "jag_get_thresholds", "jag_free", "jag_last_error", "jag_version"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return build_ext.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libjag.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_ext.LIB
+            if build_if_missing and build_ext.stale():
+                build_ext.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libjag.so is missing; build it with paper_2602_10258_gb300.build_ext")
+            L = C.CDLL(path)
+            P = C.c_void_p
+            L.jag_build.argtypes = [C.POINTER(BuildParams), C.POINTER(P)]
+            L.jag_build.restype = C.c_int
+            L.jag_search.argtypes = [P, C.POINTER(SearchArgs)]
+            L.jag_search.restype = C.c_int
+            L.jag_search_host.argtypes = [P, C.POINTER(SearchArgs)]
+            L.jag_search_host.restype = C.c_int
+            L.jag_get_info.argtypes = [P, C.POINTER(Info)]
+            L.jag_get_info.restype = C.c_int
+            L.jag_get_graph.argtypes = [P, P]
+            L.jag_get_graph.restype = C.c_int
+            L.jag_get_thresholds.argtypes = [P, P]
+            L.jag_get_thresholds.restype = C.c_int
+            L.jag_free.argtypes = [P]
+            L.jag_free.restype = None
+            L.jag_last_error.argtypes = []
+            L.jag_last_error.restype = C.c_char_p
+            L.jag_version.argtypes = []
+            L.jag_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != JAG_OK:
+        raise JagError(rc, load().jag_last_error().decode())
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def jag_build(x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=JAG_F_RANGE_I32, R=32,
+              l_b=64, alpha=1.2, thresholds=(100, 1, 0), sample_size=500, seed=0,
+              storage=JAG_VEC_F32, device=0, graph=None, entry=0):
+    """Build (or upload) an index from host arrays; returns an opaque handle."""
+    L = load()
+    x = np.ascontiguousarray(x, np.float32)
+    keep = [x]
+
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dt)
+        keep.append(a)
+        return a
+
+    ai, af, am = arr(attr_i32, np.int32), arr(attr_f32, np.float32), arr(attr_mask, np.uint64)
+    g = arr(graph, np.int32)
+    p = BuildParams()
+    p.n, p.d = x.shape
+    p.x = _np_ptr(x)
+    p.attr_i32, p.attr_f32, p.attr_mask = _np_ptr(ai), _np_ptr(af), _np_ptr(am)
+    p.dist_a, p.R, p.l_b, p.alpha = int(dist_a), int(R), int(l_b), float(alpha)
+    th = list(thresholds)
+    p.n_thresholds = len(th)
+    for i in range(min(4, len(th))):
+        p.threshold_pct[i] = int(th[i])
+    p.sample_size, p.seed, p.storage, p.device = int(sample_size), int(seed), int(storage), int(device)
+    p.graph = _np_ptr(g)
+    p.entry = int(entry)
+    h = C.c_void_p()
+    _check(L.jag_build(C.byref(p), C.byref(h)))
+    return h
+
+
+def jag_free(h):
+    if h:
+        load().jag_free(h)
+
+
+def jag_get_info(h) -> dict:
+    i = Info()
+    _check(load().jag_get_info(h, C.byref(i)))
+    return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+def jag_get_graph(h) -> np.ndarray:
+    info = jag_get_info(h)
+    out = np.empty((info["n"], info["R"]), np.int32)
+    _check(load().jag_get_graph(h, _np_ptr(out)))
+    return out
+
+
+def jag_get_thresholds(h) -> np.ndarray:
+    info = jag_get_info(h)
+    out = np.empty((info["n"], info["n_thresholds"]), np.uint32)
+    _check(load().jag_get_thresholds(h, _np_ptr(out)))
+    return out
+
+
+def _args(nq, k, beam, s0, scan_cap, flags, hash_bits, aux_bytes):
+    a = SearchArgs()
+    a.nq, a.k, a.beam = int(nq), int(k), int(beam)
+    a.s0, a.scan_cap, a.flags, a.hash_bits = int(s0), int(scan_cap), int(flags), int(hash_bits)
+    a.aux_bytes = int(aux_bytes)
+    return a
+
+
+def jag_search(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=None, stream=None,
+               s0=-1, scan_cap=0, flags=0, hash_bits=0, ev_begin=None, ev_end=None):
+    """Device-pointer search: every tensor argument is a CUDA tensor (queries
+    float32 [nq, d], filters uint8 [nq*16], aux uint8, out_ids int32 [nq, k],
+    out_dist float32 [nq, k], counters int32 [nq, 4] or None).  Asynchronous
+    on ``stream`` (a torch.cuda.Stream or None for the current stream)."""
+    import torch
+    L = load()
+    nq = queries.shape[0]
+    a = _args(nq, k, beam, s0, scan_cap, flags, hash_bits, 0 if aux is None else aux.numel())
+    a.queries = queries.data_ptr()
+    a.filters = filters.data_ptr()
+    a.filter_aux = None if aux is None or aux.numel() == 0 else aux.data_ptr()
+    a.out_ids, a.out_dist = out_ids.data_ptr(), out_dist.data_ptr()
+    a.counters = None if counters is None else counters.data_ptr()
+    st = stream if stream is not None else torch.cuda.current_stream(queries.device)
+    a.stream = st.cuda_stream
+    a.ev_graph_begin = None if ev_begin is None else ev_begin.cuda_event
+    a.ev_graph_end = None if ev_end is None else ev_end.cuda_event
+    _check(L.jag_search(h, C.byref(a)))
+
+
+def jag_search_host(h, queries, filters, aux, k, beam, counters=False, s0=-1, scan_cap=0, flags=0,
+                    hash_bits=0, out_ids=None, out_dist=None, out_counters=None):
+    """Host-buffer search: numpy (or pinned torch CPU) inputs and outputs; the
+    call copies to and from the device and returns when answers are in host
+    memory.  Returns (ids, dist, counters)."""
+    L = load()
+    q = np.ascontiguousarray(queries, np.float32) if isinstance(queries, np.ndarray) else queries
+    nq = q.shape[0]
+    f = np.ascontiguousarray(filters) if isinstance(filters, np.ndarray) else filters
+    ax = aux
+    if isinstance(aux, np.ndarray):
+        ax = np.ascontiguousarray(aux, np.uint8)
+    nb = 0 if ax is None else (ax.nbytes if isinstance(ax, np.ndarray) else ax.numel())
+
+    def ptr(t):
+        if t is None:
+            return None
+        return t.ctypes.data if isinstance(t, np.ndarray) else t.data_ptr()
+
+    if out_ids is None:
+        out_ids = np.empty((nq, k), np.int32)
+    if out_dist is None:
+        out_dist = np.empty((nq, k), np.float32)
+    cnt = out_counters
+    if counters and cnt is None:
+        cnt = np.empty((nq, 4), np.int32)
+    a = _args(nq, k, beam, s0, scan_cap, flags, hash_bits, nb)
+    a.queries, a.filters, a.filter_aux = ptr(q), ptr(f), (ptr(ax) if nb else None)
+    a.out_ids, a.out_dist, a.counters = ptr(out_ids), ptr(out_dist), ptr(cnt) if counters else None
+    a.stream = None
+    _check(L.jag_search_host(h, C.byref(a)))
+    return out_ids, out_dist, (cnt if counters else None)
+
+
+class Index:
+    """Convenience owner of a built index (frees it on close/deletion)."""
+
+    def __init__(self, x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=JAG_F_RANGE_I32, R=32,
+                 l_b=64, alpha=1.2, thresholds=(100, 1, 0), sample_size=500, seed=0,
+                 storage=JAG_VEC_F32, device=0, graph=None, entry=0):
+        self.h = jag_build(x, attr_i32, attr_f32, attr_mask, dist_a, R, l_b, alpha, thresholds,
+                           sample_size, seed, storage, device, graph, entry)
+        self.d = int(np.asarray(x).shape[1])
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.x, w.attr_i32, w.attr_f32, w.attr_mask, w.dist_a, **kw)
+
+    def info(self):
+        return jag_get_info(self.h)
+
+    def graph(self):
+        return jag_get_graph(self.h)
+
+    def thresholds(self):
+        return jag_get_thresholds(self.h)
+
+    def search(self, queries, filters, aux, k, beam, counters=False, stream=None, s0=-1, scan_cap=0,
+               flags=0, hash_bits=0, ev_begin=None, ev_end=None):
+        """Search with device tensors; filters/aux may be numpy (copied to the
+        device).  Returns CUDA tensors (ids, dist, counters or None)."""
+        import torch
+        dev = queries.device
+        ft = filters_to_device(filters, dev)
+        at = aux_to_device(aux, dev)
+        nq = queries.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev) if counters else None
+        jag_search(self.h, queries, ft, at, k, beam, ids, dist, cnt, stream, s0, scan_cap, flags,
+                   hash_bits, ev_begin, ev_end)
+        return ids, dist, cnt
+
+    def search_host(self, queries, filters, aux, k, beam, **kw):
+        return jag_search_host(self.h, queries, filters, aux, k, beam, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            jag_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def filters_to_device(filters, device):
+    import torch
+    if isinstance(filters, torch.Tensor):
+        return filters.to(device)
+    f = np.ascontiguousarray(filters, dtype=FILTER_DTYPE)
+    return torch.from_numpy(f.view(np.uint8).copy()).to(device)
+
+
+def aux_to_device(aux, device):
+    import torch
+    if aux is None:
+        return None
+    if isinstance(aux, torch.Tensor):
+        return aux.to(device)
+    return torch.from_numpy(np.ascontiguousarray(aux, np.uint8).copy()).to(device)

@@ -13,6 +13,8 @@ import pytest
 from oracle import jag_oracle as O
 from paper_2602_10258_gb300 import datagen as D
 
+from _golden import read_build_golden
+
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -275,26 +277,8 @@ def test_brute_force_short_results_padded():
 # hand-worked build and query (tests/golden/build_1d_5pts.txt)
 # ---------------------------------------------------------------------------
 
-def _read_build_golden():
-    rows, entry, query, answer = {}, None, None, None
-    for line in open(os.path.join(GOLD, "build_1d_5pts.txt")):
-        line = line.split("#")[0].strip()
-        if not line:
-            continue
-        tok = line.split()
-        if tok[0] == "entry":
-            entry = int(tok[1])
-        elif tok[0] == "row":
-            rows[int(tok[1])] = [int(t) for t in tok[2:]]
-        elif tok[0] == "query":
-            query = [float(t) for t in tok[1:]]
-        elif tok[0] == "answer":
-            answer = [float(t) for t in tok[1:]]
-    return rows, entry, query, answer
-
-
 def test_build_hand_worked_example():
-    rows, entry, query, answer = _read_build_golden()
+    rows, entry, query, answer = read_build_golden()
     x = np.array([[0], [2], [3], [7], [9]], np.float32)
     lab = np.arange(5, dtype=np.int32)
     ix = O.Index(x, attr_i32=lab, dist_a=O.K_LABEL, R=2)
