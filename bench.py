@@ -1,0 +1,480 @@
+"""Benchmark: QPS at recall@10 >= 0.95 per selectivity band, JAG filtered
+search on one GB300 (N GPUs: one replica and one query batch per rank).
+
+Workload (synthetic stand-in for the paper's label-filter datasets): N=1,000,000
+base vectors, d=128, fp32, from a 100-component Gaussian mixture (centres
+N(0,4I), unit covariance); one label per point, Zipf(1.1) over 1,000 labels;
+10,000 queries from the same mixture with labels from the same law; k=10,
+graph degree R=32, build beam 64, thresholds {100%, 0%}, alpha 1.2; labels
+with fewer than 10,000 points (selectivity < 1%) go to the exact scan.
+
+A step = one jag_search call over the whole 10,000-query batch: filter
+preparation and routing, graph search (Algorithm 2) for graph-routed
+queries, exact scan for the most selective ones.  The beam is the smallest of
+16..256 for which recall@10 (against the GPU brute-force scan) is >= 0.95 in
+every selectivity band.  Inputs (640 MB of vectors + graph) exceed the L2
+cache, and L2 is also flushed between timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10=0.95 per selectivity band; plain FP32 vs BF16+learned; p99 ms"
+BEAMS = [16, 24, 32, 48, 64, 96, 128, 192, 256]
+BANDS = [(0.0, 1e-4, "<1e-4"), (1e-4, 1e-3, "[1e-4,1e-3)"), (1e-3, 1e-2, "[1e-3,1e-2)"),
+         (1e-2, 1e-1, "[1e-2,1e-1)"), (1e-1, 1.01, "[1e-1,1]")]
+K = 10
+R = 32
+LB = 64
+THRESHOLDS = (100, 0)
+ALPHA = 1.2
+S0 = 10000
+
+
+def workload_desc(n, d, nq):
+    return "label filter, Zipf(1.1) over 1000 labels, N=%d d=%d fp32 GMM-100, %d queries, k=10, R=32" % (n, d, nq)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def rank_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def recall_at_k(ids, gt_ids, gt_d, k=K):
+    """Tie-tolerant recall@k: returned ids whose true distance is within the
+    k-th true distance count as hits; divided by min(k, #passing)."""
+    out = np.zeros(len(ids))
+    for i in range(len(ids)):
+        g = gt_ids[i][gt_ids[i] >= 0]
+        m = min(k, len(g))
+        if m == 0:
+            out[i] = np.nan
+            continue
+        out[i] = len(set(ids[i][ids[i] >= 0].tolist()) & set(g[:m].tolist())) / m
+    return out
+
+
+def band_of(sel):
+    b = np.full(len(sel), -1)
+    for j, (lo, hi, _) in enumerate(BANDS):
+        b[(sel >= lo) & (sel < hi)] = j
+    return b
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(src_hash):
+    """Per-launch DRAM bytes of the query kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "query_kernel_label_1m.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or h.group(1) != src_hash:
+        return None
+    return float(t.group(1))
+
+
+def kernel_source_hash():
+    import hashlib
+    hs = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2602_10258_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        hs.update(open(os.path.join(cs, f), "rb").read())
+    return hs.hexdigest()[:16]
+
+
+def make_workload(args):
+    from paper_2602_10258_gb300 import datagen as D
+    return D.make_label_zipf(n=args.n, d=128, nq=args.nq, seed=args.seed)
+
+
+def selectivity(w):
+    counts = np.bincount(w.attr_i32, minlength=int(w.attr_i32.max()) + 1)
+    lab = w.filters["payload"].astype(np.int64) & 0xFFFFFFFF
+    return counts[np.minimum(lab, len(counts) - 1)] / w.n
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2602_10258_gb300 import jag
+
+    rank, world, local = rank_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    w = make_workload(args)
+    sel = selectivity(w)
+    band = band_of(sel)
+    t0 = time.time()
+    idx = jag.Index.from_workload(w, R=R, l_b=LB, alpha=ALPHA, thresholds=THRESHOLDS, device=local)
+    build_s = time.time() - t0
+    info = idx.info()
+    log("build: %.2f s (GPU %.2f s), entry %d" % (build_s, info["build_seconds"], info["entry"]))
+    q = torch.from_numpy(w.q).to(dev)
+    ft = jag.filters_to_device(w.filters, dev)
+    at = jag.aux_to_device(w.aux, dev)
+    nq = w.q.shape[0]
+    stream = torch.cuda.current_stream(dev)
+
+    # ground truth by the exact scan
+    gt_ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    gt_d = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    jag.jag_search(idx.h, q, ft, at, K, K, gt_ids, gt_d, None, stream, flags=jag.JAG_SEARCH_SCAN_ALL)
+    torch.cuda.synchronize()
+    gt_ids, gt_d = gt_ids.cpu().numpy(), gt_d.cpu().numpy()
+
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev)
+    sweep = {}
+    chosen = None
+    band_min_beam = {}
+    for beam in BEAMS:
+        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy(), gt_ids, gt_d)
+        per = {}
+        for j, (_, _, name) in enumerate(BANDS):
+            m = (band == j) & ~np.isnan(rec)
+            if m.any():
+                per[name] = float(np.mean(rec[m]))
+                if per[name] >= 0.95 and name not in band_min_beam:
+                    band_min_beam[name] = beam
+        sweep[beam] = per
+        log("beam %d: %s" % (beam, {k: round(v, 4) for k, v in per.items()}))
+        if chosen is None and all(v >= 0.95 for v in per.values()):
+            chosen = beam
+            if not args.full_sweep:
+                break
+    if chosen is None:
+        chosen = BEAMS[-1]
+
+    # counters pass: algorithmic bytes of one launch (untimed)
+    jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, cnt, stream, s0=S0)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy().astype(np.int64)
+    graph_q = c[:, 3] == 0
+    scan_q = c[:, 3] == 1
+    row_bytes = 128 * 4
+    bytes_graph = int((c[graph_q, 0] * R * 4 + c[graph_q, 1] * 4 + c[graph_q, 2] * row_bytes).sum())
+    bytes_scan = int((c[scan_q, 2] * (row_bytes + 4)).sum())
+    alg_bytes = bytes_graph + bytes_scan
+
+    # timed steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for s_ev, e_ev, kb, ke in ev:   # torch creates the CUDA event on first record
+        kb.record(stream)
+        ke.record(stream)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            s_ev, e_ev, kb, ke = ev[i]
+            s_ev.record(stream)
+            jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, ev_begin=kb, ev_end=ke)
+            e_ev.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = np.array([s.elapsed_time(e) for s, e, _, _ in ev])
+    kern_ms = np.array([a.elapsed_time(b) for _, _, a, b in ev])
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nq / (ms_per_step / 1000.0)
+
+    # per-band QPS at each band's own smallest beam (informational)
+    bands_out = {}
+    for j, (_, _, name) in enumerate(BANDS):
+        sel_q = np.nonzero(band == j)[0]
+        if len(sel_q) == 0:
+            continue
+        beam_b = band_min_beam.get(name, chosen)
+        qb = q[torch.from_numpy(sel_q).to(dev)]
+        fb = jag.filters_to_device(w.filters[sel_q], dev)
+        ib = torch.empty((len(sel_q), K), dtype=torch.int32, device=dev)
+        db = torch.empty((len(sel_q), K), dtype=torch.float32, device=dev)
+        ts = []
+        for r in range(4):
+            flush.fill_(2.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            jag.jag_search(idx.h, qb, fb, at, K, beam_b, ib, db, None, stream, s0=S0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        rec = recall_at_k(ib.cpu().numpy(), gt_ids[sel_q], gt_d[sel_q])
+        bands_out[name] = {"queries": int(len(sel_q)), "beam": int(beam_b),
+                           "recall": float(np.nanmean(rec)) if np.isfinite(rec).any() else None,
+                           "qps": float(len(sel_q) / (np.median(ts) / 1000.0)),
+                           "routed_to_scan": int((c[sel_q, 3] == 1).sum())}
+
+    # end to end through the host-buffer entry point
+    pin_q = torch.from_numpy(w.q).pin_memory()
+    pin_f = torch.from_numpy(np.ascontiguousarray(w.filters).view(np.uint8).copy()).pin_memory()
+    pin_ids = torch.empty((nq, K), dtype=torch.int32).pin_memory()
+    pin_d = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        jag.jag_search_host(idx.h, pin_q, pin_f, None, K, chosen, s0=S0, out_ids=pin_ids, out_dist=pin_d)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        jag.jag_search_host(idx.h, pin_q, pin_f, None, K, chosen, s0=S0, out_ids=pin_ids, out_dist=pin_d)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_rec = recall_at_k(pin_ids.numpy(), gt_ids, gt_d)
+    assert np.array_equal(pin_ids.numpy(), ids.cpu().numpy())
+
+    peak, peak_kind = measured_peaks()
+    kavg_s = float(kern_ms.mean()) / 1000.0
+    achieved = alg_bytes / kavg_s / 1e9
+    traffic = profile_traffic(kernel_source_hash())
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "query_kernel", "kernel_ms": round(kavg_s * 1000, 3),
+                "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_kind}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(w, idx, chosen, gt_ids, gt_d, budget_s=args.cpu_seconds)
+
+    recall_chosen = sweep[chosen]
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w.n, w.d, nq), "beam": chosen, "k": K, "R": R,
+                   "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.1f" % (LB, list(THRESHOLDS), ALPHA),
+                   "build_seconds": round(build_s, 2), "index_device_bytes": info["device_bytes"],
+                   "scan_threshold_s0": S0, "l2": "inputs larger than L2 and L2 flushed between steps",
+                   "recall_at_beam": recall_chosen, "bands": bands_out,
+                   "beam_sweep": {str(b): v for b, v in sweep.items()},
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": {"value": round(nq / float(np.median(e2e_t)), 1), "unit": "queries/s",
+                "h2d_bytes_per_step": int(w.q.nbytes + w.filters.nbytes),
+                "d2h_bytes_per_step": int(nq * K * 8),
+                "recall": float(np.nanmean(e2e_rec))},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "gpu_launches": int(args.steps * 2),
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    idx.close()
+
+
+def cpu_baseline(w, idx, beam, gt_ids, gt_d, budget_s=15.0):
+    """The oracle's Query on the same graph and beam, all host cores, over a
+    bounded sample of the batch (as many 200-query slices as fit the time
+    budget)."""
+    from oracle import jag_oracle as O
+    graph = idx.graph()
+    info = idx.info()
+    ox = O.Index.from_workload(w, R=R, graph=graph, entry=info["entry"])
+    cores = os.cpu_count() or 1
+    done, t_total = 0, 0.0
+    ids_all = []
+    while done < len(w.q) and t_total < budget_s:
+        sl = slice(done, min(done + 200, len(w.q)))
+        t1 = time.perf_counter()
+        ids, _, _ = O.query(ox, w.q[sl], w.filters[sl], w.aux, K, beam, s0=S0, scan_cap=8192, nthreads=cores)
+        t_total += time.perf_counter() - t1
+        ids_all.append(ids)
+        done = sl.stop
+    ids = np.concatenate(ids_all)
+    rec = recall_at_k(ids, gt_ids[:done], gt_d[:done])
+    return {"value": round(done / t_total, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of the %d queries, beam %d, %.1f s" % (done, len(w.q), beam, t_total),
+            "recall": float(np.nanmean(rec))}
+
+
+def run_reference(args):
+    """The oracle (plain C, host cores) as the reference arm: each step times
+    Query on a bounded slice of the same batch over the same index."""
+    rank, world, local = rank_env()
+    if rank != 0:
+        return
+    import torch
+    from paper_2602_10258_gb300 import jag
+    from oracle import jag_oracle as O
+    torch.cuda.set_device(local)
+    w = make_workload(args)
+    idx = jag.Index.from_workload(w, R=R, l_b=LB, alpha=ALPHA, thresholds=THRESHOLDS, device=local)
+    graph, info = idx.graph(), idx.info()
+    idx.close()
+    ox = O.Index.from_workload(w, R=R, graph=graph, entry=info["entry"])
+    cores = os.cpu_count() or 1
+    beam = args.ref_beam
+    per = max(50, args.ref_queries)
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = (i * per) % len(w.q)
+        sl = slice(s, min(s + per, len(w.q)))
+        t1 = time.perf_counter()
+        O.query(ox, w.q[sl], w.filters[sl], w.aux, K, beam, s0=S0, scan_cap=8192, nthreads=cores)
+        dt = time.perf_counter() - t1
+        if i >= args.warmup:
+            times.append((sl.stop - sl.start, dt))
+    nq_t = sum(t[0] for t in times)
+    t_t = sum(t[1] for t in times)
+    value = nq_t / t_t
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "queries/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1000 * t_t / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload_desc(w.n, w.d, len(w.q)), "beam": beam, "k": K, "R": R,
+                      "index": "graph from the GPU build (index construction is not timed)"},
+           "cpu_baseline": {"value": round(value, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
+                            "sample": "%d queries per step, beam %d" % (per, beam)},
+           "e2e": {"value": round(value, 2), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_profile(args):
+    """Build the index and run a few searches at a fixed beam (no sweep, no
+    ground truth): the command profiled by ncu."""
+    import torch
+    from paper_2602_10258_gb300 import jag
+    torch.cuda.set_device(0)
+    w = make_workload(args)
+    idx = jag.Index.from_workload(w, R=R, l_b=LB, alpha=ALPHA, thresholds=THRESHOLDS)
+    q = torch.from_numpy(w.q).cuda()
+    ft = jag.filters_to_device(w.filters, q.device)
+    ids = torch.empty((len(w.q), K), dtype=torch.int32, device=q.device)
+    dd = torch.empty((len(w.q), K), dtype=torch.float32, device=q.device)
+    for _ in range(args.steps):
+        jag.jag_search(idx.h, q, ft, None, K, args.beam, ids, dd, None, None, s0=S0)
+    torch.cuda.synchronize()
+    log("profile run done: %d searches of %d queries at beam %d" % (args.steps, len(w.q), args.beam))
+    idx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--full-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-beam", type=int, default=192)
+    ap.add_argument("--ref-queries", type=int, default=200)
+    ap.add_argument("--profile", action="store_true", help="fixed-beam searches only (for ncu)")
+    ap.add_argument("--beam", type=int, default=192)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

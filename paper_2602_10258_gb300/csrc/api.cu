@@ -144,7 +144,9 @@ void sorted_column(const V *vals, int64_t n, std::vector<V> &sv, std::vector<int
   for (int64_t i = 0; i < n; ++i) { sv[(size_t)i] = tmp[(size_t)i].first; si[(size_t)i] = tmp[(size_t)i].second; }
 }
 
-int default_hash_bits(int ls) { return ls <= 64 ? 11 : (ls <= 128 ? 12 : 13); }
+// 2048 slots (8 KB) at every beam: a larger set costs occupancy, a smaller
+// one recomputation after it is cleared.
+int default_hash_bits(int) { return 11; }
 
 constexpr size_t kSmemLimit = 227 * 1024;
 

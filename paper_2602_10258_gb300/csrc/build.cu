@@ -191,29 +191,42 @@ build_search_kernel(DevIndex ix, int64_t pos0, int64_t nb, int nT, const uint32_
 // JointRobustPrune
 // ---------------------------------------------------------------------------
 
+// Candidate arrays of one prune: a slice of shared memory, or a per-warp
+// region of global scratch when the candidate set is larger than the slice.
 struct PruneSmem {
   uint32_t *cid;     // [cmax] candidate ids
   float *cdist;      // [cmax] d(p, candidate)
   uint64_t *skey;    // [cmax] sort keys
   uint32_t *sid;     // [cmax]
-  uint32_t *bucket;  // [64]
+  uint32_t *bucket;  // [64] (always shared)
   uint32_t *chosen;  // [64]
   uint32_t *tmp;     // [64]
 };
 
-__host__ __device__ inline size_t prune_smem_bytes(int cmax) {
-  return (size_t)cmax * (4 + 4 + 8 + 4) + 64 * 4 * 3;
-}
+__host__ __device__ inline size_t cand_bytes(int cmax) { return (size_t)cmax * (4 + 4 + 8 + 4); }
 
-__device__ inline PruneSmem carve_prune(uint8_t *base, int cmax) {
-  PruneSmem s;
+__host__ __device__ inline size_t prune_smem_bytes(int cmax) { return cand_bytes(cmax) + 64 * 4 * 3; }
+
+__device__ inline void carve_cands(uint8_t *base, int cmax, PruneSmem &s) {
   s.skey = reinterpret_cast<uint64_t *>(base);
   s.cid = reinterpret_cast<uint32_t *>(base + (size_t)cmax * 8);
   s.cdist = reinterpret_cast<float *>(s.cid + cmax);
   s.sid = reinterpret_cast<uint32_t *>(s.cdist + cmax);
+}
+
+__device__ inline PruneSmem carve_prune(uint8_t *base, int cmax) {
+  PruneSmem s;
+  carve_cands(base, cmax, s);
   s.bucket = s.sid + cmax;
   s.chosen = s.bucket + 64;
   s.tmp = s.chosen + 64;
+  return s;
+}
+
+// The same small arrays, candidate arrays moved to global scratch.
+__device__ inline PruneSmem spill_prune(const PruneSmem &sm, uint8_t *gbase, int cmax_g) {
+  PruneSmem s = sm;
+  carve_cands(gbase, cmax_g, s);
   return s;
 }
 
@@ -289,55 +302,62 @@ template <int P, int CPL>
 __global__ void __launch_bounds__(kPruneWarps * 32)
 prune_insert_kernel(DevIndex ix, int32_t *graph, int64_t pos0, int64_t nb, int nT, const uint32_t *thr,
                     float alpha2, const uint32_t *vis_ids, const float *vis_d, const int32_t *vis_n, int vcap,
-                    int cmax, int32_t *etgt, int32_t *esrc, uint32_t *status) {
+                    int cmax_s, int cmax_g, uint8_t *gscratch, int32_t *etgt, int32_t *esrc, uint32_t *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const PruneSmem S = carve_prune(smem + warp * prune_smem_bytes(cmax), cmax);
-  const int64_t bi = (int64_t)blockIdx.x * kPruneWarps + warp;
-  if (bi >= nb) return;
-  const int64_t p = order_id(pos0 + bi, ix.entry);
-  int nc = 0;
-  for (int ti = 0; ti < nT; ++ti) {
-    const int64_t it = bi * nT + ti;
-    const int m = min(vis_n[it], vcap);
-    for (int i = lane; i < m; i += 32) {
-      S.skey[nc + i] = make_key(0u, vis_d[it * vcap + i]);
-      S.sid[nc + i] = vis_ids[it * vcap + i];
+  const PruneSmem Ss = carve_prune(smem + warp * prune_smem_bytes(cmax_s), cmax_s);
+  const int64_t gw = (int64_t)blockIdx.x * kPruneWarps + warp;
+  const PruneSmem Sg = spill_prune(Ss, gscratch + gw * cand_bytes(cmax_g), cmax_g);
+  for (int64_t bi = gw; bi < nb; bi += (int64_t)gridDim.x * kPruneWarps) {
+    const int64_t p = order_id(pos0 + bi, ix.entry);
+    int total = 0;
+    for (int ti = 0; ti < nT; ++ti) total += min(vis_n[bi * nT + ti], vcap);
+    const PruneSmem &S = total <= cmax_s ? Ss : Sg;
+    const int cmax = total <= cmax_s ? cmax_s : cmax_g;
+    int nc = 0;
+    for (int ti = 0; ti < nT; ++ti) {
+      const int64_t it = bi * nT + ti;
+      const int m = min(vis_n[it], vcap);
+      for (int i = lane; i < m; i += 32) {
+        S.skey[nc + i] = make_key(0u, vis_d[it * vcap + i]);
+        S.sid[nc + i] = vis_ids[it * vcap + i];
+      }
+      nc += m;
     }
-    nc += m;
-  }
-  const int M = next_pow2(nc > 0 ? nc : 1);
-  for (int i = nc + lane; i < M; i += 32) { S.skey[i] = kNoKey; S.sid[i] = kEmptySlot; }
-  __syncwarp();
-  warp_sort_smem(S.skey, S.sid, M);
-  // drop repeats (equal id means equal distance: adjacent after the sort)
-  int w = 0;
-  for (int b = 0; b < nc; b += 32) {
-    const int i = b + lane;
-    uint64_t k = kNoKey;
-    uint32_t id = kEmptySlot;
-    bool keep = false;
-    if (i < nc) {
-      k = S.skey[i];
-      id = S.sid[i];
-      keep = (i == 0) || (S.sid[i - 1] != id);
-    }
-    const uint32_t m = __ballot_sync(kFull, keep);
+    const int M = next_pow2(nc > 0 ? nc : 1);
+    for (int i = nc + lane; i < M; i += 32) { S.skey[i] = kNoKey; S.sid[i] = kEmptySlot; }
     __syncwarp();
-    if (keep) {
-      const int pos = w + __popc(m & lanemask_lt());
-      S.cid[pos] = id;
-      S.cdist[pos] = u2f((uint32_t)k);
+    warp_sort_smem(S.skey, S.sid, M);
+    // drop repeats (equal id means equal distance: adjacent after the sort)
+    int w = 0;
+    for (int b = 0; b < nc; b += 32) {
+      const int i = b + lane;
+      uint64_t k = kNoKey;
+      uint32_t id = kEmptySlot;
+      bool keep = false;
+      if (i < nc) {
+        k = S.skey[i];
+        id = S.sid[i];
+        keep = (i == 0) || (S.sid[i - 1] != id);
+      }
+      const uint32_t m = __ballot_sync(kFull, keep);
+      __syncwarp();
+      if (keep) {
+        const int pos = w + __popc(m & lanemask_lt());
+        S.cid[pos] = id;
+        S.cdist[pos] = u2f((uint32_t)k);
+      }
+      w += __popc(m);
     }
-    w += __popc(m);
-  }
-  __syncwarp();
-  int32_t *row = graph + p * ix.R;
-  joint_prune<P, CPL>(ix, p, S, w, cmax, thr + p * nT, nT, alpha2, row);
-  for (int r = lane; r < ix.R; r += 32) {
-    const int32_t v = row[r];
-    etgt[bi * ix.R + r] = v;
-    esrc[bi * ix.R + r] = v >= 0 ? (int32_t)p : -1;
+    __syncwarp();
+    int32_t *row = graph + p * ix.R;
+    joint_prune<P, CPL>(ix, p, S, w, cmax, thr + p * nT, nT, alpha2, row);
+    for (int r = lane; r < ix.R; r += 32) {
+      const int32_t v = row[r];
+      etgt[bi * ix.R + r] = v;
+      esrc[bi * ix.R + r] = v >= 0 ? (int32_t)p : -1;
+    }
+    __syncwarp();
   }
 }
 
@@ -380,11 +400,13 @@ __global__ void edge_scatter_kernel(const int32_t *etgt, const int32_t *esrc, in
 template <int P, int CPL>
 __global__ void __launch_bounds__(kPruneWarps * 32)
 edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, const uint32_t *thr, float alpha2,
-                  int cmax, EdgeState E, uint32_t *status) {
+                  int cmax_s, int cmax_g, uint8_t *gscratch, EdgeState E, uint32_t *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const PruneSmem S = carve_prune(smem + warp * prune_smem_bytes(cmax), cmax);
-  for (int64_t i = (int64_t)blockIdx.x * kPruneWarps + warp; i < cap_targets; i += (int64_t)gridDim.x * kPruneWarps) {
+  const PruneSmem Ss = carve_prune(smem + warp * prune_smem_bytes(cmax_s), cmax_s);
+  const int64_t gw = (int64_t)blockIdx.x * kPruneWarps + warp;
+  const PruneSmem Sg = spill_prune(Ss, gscratch + gw * cand_bytes(cmax_g), cmax_g);
+  for (int64_t i = gw; i < cap_targets; i += (int64_t)gridDim.x * kPruneWarps) {
     if ((unsigned long long)i >= E.ctr[0]) return;
     const int32_t v = E.tlist[i];
     const int ns = E.tcount[v];
@@ -394,7 +416,9 @@ edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, cons
     for (int r = lane; r < ix.R; r += 32) deg += row[r] >= 0 ? 1 : 0;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) deg += __shfl_xor_sync(kFull, deg, o);
-    if (deg + ns > cmax) {
+    const PruneSmem &S = deg + ns <= cmax_s ? Ss : Sg;
+    const int cmax = deg + ns <= cmax_s ? cmax_s : cmax_g;
+    if (deg + ns > cmax_g) {
       if (lane == 0) atomicOr(status, kErrCandOverflow);
     } else if (deg + ns <= ix.R) {
       // append the new sources in increasing id order
@@ -443,7 +467,9 @@ struct BuildScratch {
   uint32_t *status = nullptr;
   double *centroid = nullptr;
   unsigned long long *best = nullptr;
-  void *blocks[16] = {};
+  uint8_t *gscratch = nullptr;   // per-warp candidate arrays of large prunes
+  int64_t prune_blocks = 0;
+  void *blocks[24] = {};
   int nblocks = 0;
 };
 
@@ -476,13 +502,14 @@ static cudaError_t launch_build_search(const BuildLaunch &B, int64_t pos0, int64
 
 template <int P, int CPL>
 static cudaError_t launch_prunes(const BuildLaunch &B, int64_t pos0, int64_t nb, BuildScratch &s, int vcap,
-                                 int cmax) {
-  const size_t smem = (size_t)kPruneWarps * prune_smem_bytes(cmax);
+                                 int cmax_s, int cmax_g) {
+  const size_t smem = (size_t)kPruneWarps * prune_smem_bytes(cmax_s);
   auto pk = prune_insert_kernel<P, CPL>;
   cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  pk<<<(unsigned)((nb + kPruneWarps - 1) / kPruneWarps), kPruneWarps * 32, smem, B.stream>>>(
-      B.ix, B.graph, pos0, nb, B.nT, B.thr, B.alpha2, s.vis_ids, s.vis_d, s.vis_n, vcap, cmax, s.etgt, s.esrc,
-      s.status);
+  const int64_t pgrid = std::min<int64_t>((nb + kPruneWarps - 1) / kPruneWarps, s.prune_blocks);
+  pk<<<(unsigned)std::max<int64_t>(pgrid, 1), kPruneWarps * 32, smem, B.stream>>>(
+      B.ix, B.graph, pos0, nb, B.nT, B.thr, B.alpha2, s.vis_ids, s.vis_d, s.vis_n, vcap, cmax_s, cmax_g,
+      s.gscratch, s.etgt, s.esrc, s.status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t ne = nb * B.ix.R;
@@ -492,23 +519,20 @@ static cudaError_t launch_prunes(const BuildLaunch &B, int64_t pos0, int64_t nb,
   edge_scatter_kernel<<<eb, 256, 0, B.stream>>>(s.etgt, s.esrc, ne, s.E);
   auto ak = edge_apply_kernel<P, CPL>;
   cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ak, kPruneWarps * 32, smem);
-  if (bps <= 0) return cudaErrorInvalidConfiguration;
-  const int64_t grid = std::min<int64_t>((int64_t)bps * dev_sms() * 4, (ne + kPruneWarps - 1) / kPruneWarps);
-  ak<<<(unsigned)std::max<int64_t>(grid, 1), kPruneWarps * 32, smem, B.stream>>>(B.ix, B.graph, ne, B.nT, B.thr,
-                                                                                  B.alpha2, cmax, s.E, s.status);
+  const int64_t agrid = std::min<int64_t>((ne + kPruneWarps - 1) / kPruneWarps, s.prune_blocks);
+  ak<<<(unsigned)std::max<int64_t>(agrid, 1), kPruneWarps * 32, smem, B.stream>>>(
+      B.ix, B.graph, ne, B.nT, B.thr, B.alpha2, cmax_s, cmax_g, s.gscratch, s.E, s.status);
   return cudaGetLastError();
 }
 
 template <int CAP>
 static cudaError_t dispatch_build(const BuildLaunch &B, int P, int CPL, int64_t pos0, int64_t nb, int hbits,
-                                  BuildScratch &s, int vcap, int cmax) {
+                                  BuildScratch &s, int vcap, int cmax_s, int cmax_g) {
   cudaError_t e = cudaErrorInvalidValue;
 #define JAG_BCASE(PP, CC)                                                   \
   if (P == PP && CPL == CC) {                                               \
     e = launch_build_search<CAP, PP, CC>(B, pos0, nb, hbits, s, vcap);      \
-    if (e == cudaSuccess) e = launch_prunes<PP, CC>(B, pos0, nb, s, vcap, cmax); \
+    if (e == cudaSuccess) e = launch_prunes<PP, CC>(B, pos0, nb, s, vcap, cmax_s, cmax_g); \
     return e;                                                               \
   }
   JAG_BCASE(8, 1)
@@ -531,8 +555,13 @@ int run_build(BuildLaunch &B, int32_t *entry_out, char *msg, size_t msg_len) {
   BuildScratch s;
   cudaError_t e = cudaSuccess;
   const int64_t bcap = std::max<int64_t>(1, n / 50);
-  const int vcap = std::max(256, 4 * B.lb);
-  const int cmax = std::max(1024, next_pow2(B.nT * vcap));
+  // visited lists: hop counts are ~l_b plus a few, but a search may expand
+  // more; 16 l_b leaves a wide margin and an overflow is reported, not cut
+  const int vcap = std::max(1024, 16 * B.lb);
+  const int cmax_s = 1024;                                   // shared-memory slice
+  const int cmax_g = std::max(8192, next_pow2(B.nT * vcap)); // global spill
+  const int blocks_per_sm = (int)std::max<size_t>(1, (227 * 1024) / (kPruneWarps * prune_smem_bytes(cmax_s)));
+  s.prune_blocks = (int64_t)blocks_per_sm * dev_sms();
   const int hbits = B.lb <= 64 ? 11 : (B.lb <= 128 ? 12 : 13);
 #define JAG_TRY(x) do { e = (x); if (e != cudaSuccess) goto fail; } while (0)
   JAG_TRY(balloc(s, (void **)&s.vis_ids, sizeof(uint32_t) * (size_t)bcap * B.nT * vcap));
@@ -550,6 +579,7 @@ int run_build(BuildLaunch &B, int32_t *entry_out, char *msg, size_t msg_len) {
   JAG_TRY(balloc(s, (void **)&s.status, 256));
   JAG_TRY(balloc(s, (void **)&s.centroid, sizeof(double) * (size_t)B.ix.d));
   JAG_TRY(balloc(s, (void **)&s.best, 256));
+  JAG_TRY(balloc(s, (void **)&s.gscratch, cand_bytes(cmax_g) * (size_t)s.prune_blocks * kPruneWarps));
   JAG_TRY(cudaMemsetAsync(s.E.tcount, 0, sizeof(int32_t) * (size_t)n, B.stream));
   JAG_TRY(cudaMemsetAsync(s.E.tfill, 0, sizeof(int32_t) * (size_t)n, B.stream));
   JAG_TRY(cudaMemsetAsync(s.status, 0, 256, B.stream));
@@ -579,9 +609,9 @@ int run_build(BuildLaunch &B, int32_t *entry_out, char *msg, size_t msg_len) {
       JAG_TRY(cudaMemsetAsync(s.work, 0, 256, B.stream));
       JAG_TRY(cudaMemsetAsync(s.E.ctr, 0, 256, B.stream));
       switch (cap_list) {
-        case 64: e = dispatch_build<64>(B, P, CPL, pos, nb, hbits, s, vcap, cmax); break;
-        case 128: e = dispatch_build<128>(B, P, CPL, pos, nb, hbits, s, vcap, cmax); break;
-        default: e = dispatch_build<256>(B, P, CPL, pos, nb, hbits, s, vcap, cmax); break;
+        case 64: e = dispatch_build<64>(B, P, CPL, pos, nb, hbits, s, vcap, cmax_s, cmax_g); break;
+        case 128: e = dispatch_build<128>(B, P, CPL, pos, nb, hbits, s, vcap, cmax_s, cmax_g); break;
+        default: e = dispatch_build<256>(B, P, CPL, pos, nb, hbits, s, vcap, cmax_s, cmax_g); break;
       }
       if (e != cudaSuccess) goto fail;
       pos += nb;
@@ -596,7 +626,7 @@ int run_build(BuildLaunch &B, int32_t *entry_out, char *msg, size_t msg_len) {
       return JAG_EUNSUPPORTED;
     }
     if (status & kErrCandOverflow) {
-      snprintf(msg, msg_len, "back-edge candidates exceeded %d", cmax);
+      snprintf(msg, msg_len, "back-edge candidates exceeded %d", cmax_g);
       return JAG_EUNSUPPORTED;
     }
     return JAG_OK;

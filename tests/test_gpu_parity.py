@@ -41,7 +41,9 @@ def assert_parity(ids, dist, rids, rdist, what=""):
         what, (~same).sum(), len(same), bad, ids[bad[:1]], rids[bad[:1]])
     m = same[:, None] & (rids >= 0)
     np.testing.assert_allclose(dist[m], rdist[m], rtol=DIST_RTOL)
-    assert (dist[m] == rdist[m]).mean() >= 0.999
+    if m.any():
+        assert (dist[m] == rdist[m]).mean() >= 0.999
+    assert np.isinf(dist[same[:, None] & (rids < 0)]).all()
 
 
 # ---------------------------------------------------------------------------
