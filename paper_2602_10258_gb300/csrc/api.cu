@@ -144,9 +144,9 @@ void sorted_column(const V *vals, int64_t n, std::vector<V> &sv, std::vector<int
   for (int64_t i = 0; i < n; ++i) { sv[(size_t)i] = tmp[(size_t)i].first; si[(size_t)i] = tmp[(size_t)i].second; }
 }
 
-// 2048 slots (8 KB) at every beam: a larger set costs occupancy, a smaller
+// 1024 slots (4 KB) at every beam: a larger set costs occupancy, a smaller
 // one recomputation after it is cleared.
-int default_hash_bits(int) { return 11; }
+int default_hash_bits(int) { return 10; }
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -162,8 +162,7 @@ jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
   if (a->nq > (int64_t)1 << 31) return fail(JAG_EINVAL, "nq too large");
   int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
   if (hb < 5 || hb > 16) return fail(JAG_EINVAL, "hash_bits must be in [5, 16]");
-  const int cap = jag::list_capacity(a->beam);
-  if ((size_t)jag::kSearchWarps * jag::warp_smem_bytes(cap, hb) > kSmemLimit)
+  if ((size_t)jag::kSearchWarps * jag::warp_smem_bytes(jag::list_slots(a->beam), hb) > kSmemLimit)
     return fail(JAG_EINVAL, "hash_bits too large for the beam");
   return JAG_OK;
 }

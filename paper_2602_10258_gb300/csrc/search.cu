@@ -245,62 +245,81 @@ __device__ int scan_candidates(const DevIndex &ix, const float4 (&q)[CPL], const
       cv = S.cid[lane];
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
-    warp_sort32(ck, cv);
-    __syncwarp();
     int r0;
-    cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, k, ck, cv, r0);
+    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
   }
   return cnt;
 }
 
-// K1/K3: each warp takes queries from a global counter; a graph-routed query
-// runs GreedySearch with D_F (Algorithm 2), a scan-routed one the exact scan
-// over its passing slice or list.
+// K1: each warp takes queries from a global counter and runs GreedySearch
+// with D_F (Algorithm 2) for the graph-routed ones.
 template <int CAP, int P, int CPL>
 __global__ void __launch_bounds__(kSearchWarps * 32)
 query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
-             const uint8_t *lut_base, const int32_t *lists, int64_t cap, int64_t nq, int k, int ls, int hbits,
-             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work) {
+             const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int32_t *out_ids, float *out_dist,
+             int32_t *counters, unsigned long long *work) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(CAP, hbits), CAP, hbits);
+  const int lcap = list_slots(ls);
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, hbits), lcap, hbits);
   for (;;) {
     unsigned long long qi = 0;
     if (lane == 0) qi = atomicAdd(work, 1ull);
     qi = __shfl_sync(kFull, qi, 0);
     if (qi >= (unsigned long long)nq) return;
     const QueryPlan pl = plans[qi];
-    if (pl.route == kRouteSkip || pl.route > kRouteSkip) continue;
+    if (pl.route != kRouteGraph) continue;
     float4 q[CPL];
     load_point<P, CPL>(queries + (int64_t)qi * d, d, q);
-    if (pl.route == kRouteGraph) {
-      const jag_filter f = filters[qi];
-      const QueryKey key{f.kind, f.payload, pl.lut_off >= 0 ? lut_base + pl.lut_off : nullptr};
-      NoSink sink;
-      SearchStats st;
-      const int cnt = greedy_search<CAP, P, CPL>(ix, key, q, ls, hbits, S, sink, st);
-      write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
-      if (counters && lane == 0) {
-        int32_t *c = counters + qi * 4;
-        c[0] = st.hops; c[1] = st.seen; c[2] = st.dcs; c[3] = 0;
-      }
+    const jag_filter f = filters[qi];
+    const QueryKey key{f.kind, f.payload, pl.lut_off >= 0 ? lut_base + pl.lut_off : nullptr};
+    NoSink sink;
+    SearchStats st;
+    const int cnt = greedy_search<CAP, P, CPL>(ix, key, q, ls, hbits, S, sink, st);
+    write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
+    if (counters && lane == 0) {
+      int32_t *c = counters + qi * 4;
+      c[0] = st.hops; c[1] = st.seen; c[2] = st.dcs; c[3] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+// K3: exact scan of the scan-routed queries over their passing slice (label
+// and range filters) or gathered list (subset and boolean filters).
+template <int CAP, int P, int CPL>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+scan_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
+            const int32_t *lists, int64_t cap, int64_t nq, int k, int32_t *out_ids, float *out_dist,
+            int32_t *counters, unsigned long long *work) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lcap = list_slots(k);
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, 5), lcap, 5);
+  for (;;) {
+    unsigned long long qi = 0;
+    if (lane == 0) qi = atomicAdd(work, 1ull);
+    qi = __shfl_sync(kFull, qi, 0);
+    if (qi >= (unsigned long long)nq) return;
+    const QueryPlan pl = plans[qi];
+    if (pl.route != kRouteSlice && pl.route != kRouteList) continue;
+    float4 q[CPL];
+    load_point<P, CPL>(queries + (int64_t)qi * d, d, q);
+    const int32_t *ids;
+    int64_t m;
+    if (pl.route == kRouteSlice) {
+      const int32_t kind = filters[qi].kind;
+      ids = (kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
+      m = pl.end - pl.begin;
     } else {
-      const int32_t *ids;
-      int64_t m;
-      if (pl.route == kRouteSlice) {
-        const int32_t kind = filters[qi].kind;
-        ids = (kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
-        m = pl.end - pl.begin;
-      } else {
-        ids = lists + (int64_t)qi * cap;
-        m = pl.count;
-      }
-      const int cnt = scan_candidates<CAP, P, CPL>(ix, q, ids, m, k, S);
-      write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
-      if (counters && lane == 0) {
-        int32_t *c = counters + qi * 4;
-        c[0] = 0; c[1] = 0; c[2] = (int32_t)m; c[3] = 1;
-      }
+      ids = lists + (int64_t)qi * cap;
+      m = pl.count;
+    }
+    const int cnt = scan_candidates<CAP, P, CPL>(ix, q, ids, m, k, S);
+    write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
+    if (counters && lane == 0) {
+      int32_t *c = counters + qi * 4;
+      c[0] = 0; c[1] = 0; c[2] = (int32_t)m; c[3] = 1;
     }
     __syncwarp();
   }
@@ -350,10 +369,8 @@ brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fi
       cv = S.cid[lane];
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
-    warp_sort32(ck, cv);
-    __syncwarp();
     int r0;
-    cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, k, ck, cv, r0);
+    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
   }
   for (int j = lane; j < k; j += 32) {
     pk[j] = j < cnt ? S.bkey[j] : kNoKey;
@@ -381,10 +398,8 @@ merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const 
         cv = part_id[(qi * ntiles + t) * k + b + lane];
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
-      warp_sort32(ck, cv);
-      __syncwarp();
       int r0;
-      cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, k, ck, cv, r0);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -463,17 +478,28 @@ static int num_sms() {
 
 template <int CAP, int P, int CPL>
 static cudaError_t launch_query(const SearchLaunch &L) {
-  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(CAP, L.hbits);
+  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.ls), L.hbits);
   auto kern = query_kernel<CAP, P, CPL>;
   const int bps = blocks_per_sm(kern, smem);
   if (bps == 0) return cudaErrorInvalidConfiguration;
-  int64_t want = (L.nq + kSearchWarps - 1) / kSearchWarps;
-  int64_t grid = std::min<int64_t>((int64_t)bps * num_sms(), std::max<int64_t>(want, 1));
+  const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
+  const int64_t grid = std::min<int64_t>((int64_t)bps * num_sms(), want);
   if (L.ev_begin) cudaEventRecord(L.ev_begin, L.stream);
-  kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(
-      L.ix, L.queries, L.d, L.filters, L.plans, L.lut, L.lists, L.cap, L.nq, L.k, L.ls, L.hbits, L.out_ids,
-      L.out_dist, L.counters, L.work);
+  kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lut,
+                                                             L.nq, L.k, L.ls, L.hbits, L.out_ids, L.out_dist,
+                                                             L.counters, L.work);
   if (L.ev_end) cudaEventRecord(L.ev_end, L.stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || L.s0 <= 0) return e;
+  // the exact scan for the routed queries (k <= ls <= CAP)
+  const size_t ssm = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.k), 5);
+  auto sk = scan_kernel<CAP, P, CPL>;
+  const int sbps = blocks_per_sm(sk, ssm);
+  if (sbps == 0) return cudaErrorInvalidConfiguration;
+  const int64_t sgrid = std::min<int64_t>((int64_t)sbps * num_sms(), want);
+  sk<<<(unsigned)sgrid, kSearchWarps * 32, ssm, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lists,
+                                                           L.cap, L.nq, L.k, L.out_ids, L.out_dist, L.counters,
+                                                           L.work + 1);
   return cudaGetLastError();
 }
 

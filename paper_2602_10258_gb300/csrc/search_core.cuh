@@ -17,9 +17,11 @@
 //            elements of a chunk in order by fma, then the butterfly
 //            acc_l + acc_(l xor o) for o = 16..1 (groups of P < 32 lanes only
 //            skip steps that would add exact zeros);
-//   merge    warp bitonic sort of the <= 32 new keys, then an in-place merge
-//            into L that keeps the best l_s and drops a neighbour already in
-//            L (equal key and id);
+//   merge    each surviving neighbour's position in the merged list is its
+//            rank in L (a fixed-step binary search) plus the number of
+//            smaller new keys; entries of L move right in 32-wide chunks
+//            taken from the back; the best l_s are kept and a neighbour
+//            already in L (equal key and id) is dropped;
 // until every entry of L is expanded.
 //
 // The visited set may forget (it is cleared when three quarters full): that
@@ -43,6 +45,9 @@ struct WarpSmem {
   uint32_t *rank;   // [32] merge ranks
 };
 
+// Slots of a warp's list for beam ls: ls rounded up to a multiple of 32.
+__host__ __device__ inline int list_slots(int ls) { return (ls + 31) & ~31; }
+
 __host__ __device__ inline size_t warp_smem_bytes(int cap, int hbits) {
   return (size_t)cap * 12 + ((size_t)4 << hbits) + 32 * 4 * 3;
 }
@@ -56,24 +61,6 @@ __device__ inline WarpSmem carve_warp_smem(uint8_t *base, int cap, int hbits) {
   s.ck1 = s.cid + 32;
   s.rank = s.ck1 + 32;
   return s;
-}
-
-// Ascending bitonic sort of one (key, id) pair per lane.
-__device__ __forceinline__ void warp_sort32(uint64_t &key, uint32_t &id) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      uint64_t ok = __shfl_xor_sync(kFull, key, j);
-      uint32_t oi = __shfl_xor_sync(kFull, id, j);
-      bool up = (lane & k) == 0;
-      bool lower = (lane & j) == 0;
-      bool other_less = key_less(ok, oi, key, id);
-      bool take = (lower == up) ? other_less : !other_less;
-      if (take) { key = ok; id = oi; }
-    }
-  }
 }
 
 __device__ __forceinline__ int first_unexpanded(const uint32_t *bid, int cnt, int start) {
@@ -102,62 +89,63 @@ __device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t 
   return true;
 }
 
-// Merge the lane-held sorted candidates (invalid = kNoKey) into L[0..cnt):
-// keep the best ls, drop candidates already present.  Returns the new count;
-// r0 receives the smallest insertion position (cnt if none).
+// Number of entries of the sorted list L[0..cnt) that precede (k, id): a
+// binary search with a fixed number of steps, so that every lane runs the
+// same instructions.
 template <int CAP>
-__device__ __forceinline__ int merge_into_list(uint64_t *bkey, uint32_t *bid, uint32_t *s_rank, int cnt,
-                                               int ls, uint64_t ck, uint32_t cidv, int &r0) {
+__device__ __forceinline__ int list_rank(const uint64_t *bkey, const uint32_t *bid, int cnt, uint64_t k,
+                                         uint32_t id) {
+  int pos = 0;
+#pragma unroll
+  for (int step = CAP; step >= 1; step >>= 1) {
+    const int probe = pos + step;
+    const int j = max(min(probe, cnt) - 1, 0);
+    const bool before = probe <= cnt && key_less(bkey[j], bid[j] & ~kExpanded, k, id);
+    pos = before ? probe : pos;
+  }
+  return pos;
+}
+
+// Merge the lane-held candidates (any order; invalid = kNoKey, distinct ids)
+// into L[0..cnt): keep the best ls, drop candidates already in L.  Returns
+// the new count; r0 receives the smallest insertion position (cnt if none).
+template <int CAP>
+__device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, int cnt, int ls, uint64_t ck,
+                                                uint32_t cv, int &r0) {
   const int lane = threadIdx.x & 31;
   bool valid = ck != kNoKey;
-  int rank = 0;
+  const int rank = list_rank<CAP>(bkey, bid, cnt, ck, cv);
   if (valid) {
-    int lo = 0, hi = cnt;
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (key_less(bkey[mid], bid[mid] & ~kExpanded, ck, cidv)) lo = mid + 1;
-      else hi = mid;
-    }
-    rank = lo;
     if (rank >= ls) valid = false;
-    else if (rank < cnt && bkey[rank] == ck && (bid[rank] & ~kExpanded) == cidv) valid = false;
+    else if (rank < cnt && bkey[rank] == ck && (bid[rank] & ~kExpanded) == cv) valid = false;
   }
   const uint32_t vm = __ballot_sync(kFull, valid);
   r0 = cnt;
   if (vm == 0) return cnt;
-  const int nv = __popc(vm);
-  const int vi = __popc(vm & lanemask_lt());
-  if (valid) s_rank[vi] = (uint32_t)rank;
-  r0 = __shfl_sync(kFull, rank, __ffs(vm) - 1);
-  constexpr int PER = CAP / 32;
-  uint64_t ek[PER];
-  uint32_t ei[PER];
-#pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    int j = r0 + lane + 32 * t;
-    if (j < cnt) { ek[t] = bkey[j]; ei[t] = bid[j]; }
+  int crank = 0;   // new keys smaller than this one
+  for (uint32_t m = vm; m; m &= m - 1) {
+    const int src = __ffs(m) - 1;
+    const uint64_t ok = __shfl_sync(kFull, ck, src);
+    const uint32_t oi = __shfl_sync(kFull, cv, src);
+    crank += key_less(ok, oi, ck, cv) ? 1 : 0;
   }
+  r0 = (int)__reduce_min_sync(kFull, valid ? (unsigned)rank : 0xFFFFFFFFu);
+  // entry j moves right by the number of new keys ranked at or before j;
+  // chunks from the back never overwrite an entry not yet read
+  for (int t = (cnt - r0 + 31) / 32 - 1; t >= 0; --t) {
+    const int j = r0 + 32 * t + lane;
+    uint64_t ek = 0;
+    uint32_t ei = 0;
+    if (j < cnt) { ek = bkey[j]; ei = bid[j]; }
+    int sh = 0;
+    for (uint32_t m = vm; m; m &= m - 1) sh += (__shfl_sync(kFull, rank, __ffs(m) - 1) <= j) ? 1 : 0;
+    __syncwarp();
+    if (j < cnt && j + sh < ls) { bkey[j + sh] = ek; bid[j + sh] = ei; }
+    __syncwarp();
+  }
+  if (valid && rank + crank < ls) { bkey[rank + crank] = ck; bid[rank + crank] = cv; }
   __syncwarp();
-#pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    int j = r0 + lane + 32 * t;
-    if (j < cnt) {
-      int lo = 0, hi = nv;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((int)s_rank[mid] <= j) lo = mid + 1;
-        else hi = mid;
-      }
-      int np = j + lo;
-      if (np < ls) { bkey[np] = ek[t]; bid[np] = ei[t]; }
-    }
-  }
-  if (valid) {
-    int np = vi + rank;
-    if (np < ls) { bkey[np] = ck; bid[np] = cidv; }
-  }
-  __syncwarp();
-  int n2 = cnt + nv;
+  const int n2 = cnt + __popc(vm);
   return n2 < ls ? n2 : ls;
 }
 
@@ -166,8 +154,8 @@ __device__ __forceinline__ int merge_into_list(uint64_t *bkey, uint32_t *bid, ui
 template <int P, int CPL>
 __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const float4 (&q)[CPL],
                                                      const uint32_t *cid, int nc) {
-  constexpr int VPW = 32 / P;                 // rows per warp-wide load
-  constexpr int U = (VPW * 8 <= 32) ? 8 / VPW : 1;   // loads in flight per lane
+  constexpr int VPW = 32 / P;                     // rows per warp-wide load
+  constexpr int U = VPW >= 4 ? 1 : 4 / VPW;       // loads in flight per lane (4 rows per warp)
   const int lane = threadIdx.x & 31;
   const int grp = lane / P, lig = lane % P;
   float mine = 0.f;
@@ -175,24 +163,28 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const f
     float4 xv[U][CPL];
 #pragma unroll
     for (int s = 0; s < U; ++s) {
-      const int c = base + s * VPW + grp;
-      const bool ok = c < nc;
-      const float *row = ix.x + (int64_t)(ok ? cid[c] : 0u) * ix.xs;
+      if (base + s * VPW < nc) {   // warp-uniform
+        const int c = base + s * VPW + grp;
+        const bool ok = c < nc;
+        const float *row = ix.x + (int64_t)(ok ? cid[c] : 0u) * ix.xs;
 #pragma unroll
-      for (int j = 0; j < CPL; ++j) {
-        const int ch = lig + j * 32;
-        xv[s][j] = (ok && ch < ix.nchunks) ? ld_chunk(row + ch * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < CPL; ++j) {
+          const int ch = lig + j * 32;
+          xv[s][j] = (ok && ch < ix.nchunks) ? ld_chunk(row + ch * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
     }
 #pragma unroll
     for (int s = 0; s < U; ++s) {
-      float acc = 0.f;
+      if (base + s * VPW < nc) {   // warp-uniform
+        float acc = 0.f;
 #pragma unroll
-      for (int j = 0; j < CPL; ++j) acc = chunk_accumulate(acc, q[j], xv[s][j]);
-      acc = group_reduce<P>(acc);
-      const int c0 = base + s * VPW;
-      const float v = __shfl_sync(kFull, acc, ((lane - c0) * P) & 31);
-      if (lane >= c0 && lane < c0 + VPW) mine = v;
+        for (int j = 0; j < CPL; ++j) acc = chunk_accumulate(acc, q[j], xv[s][j]);
+        acc = group_reduce<P>(acc);
+        const int c0 = base + s * VPW;
+        const float v = __shfl_sync(kFull, acc, ((lane - c0) * P) & 31);
+        if (lane >= c0 && lane < c0 + VPW) mine = v;
+      }
     }
   }
   return mine;
@@ -318,10 +310,8 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4
         cv = S.cid[lane];
         if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
       }
-      warp_sort32(ck, cv);
-      __syncwarp();
       int r0;
-      cnt = merge_into_list<CAP>(S.bkey, S.bid, S.rank, cnt, ls, ck, cv, r0);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0);
       rmin = r0 < rmin ? r0 : rmin;
     }
     start = (sel + 1) < rmin ? (sel + 1) : rmin;
