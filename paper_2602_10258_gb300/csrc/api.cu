@@ -299,6 +299,17 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
     ix.entry = entry;
     I->build_seconds = std::chrono::duration<double>(t1 - t0).count();
   }
+  {
+    int32_t *ea_i32 = nullptr;
+    float *ea_f32 = nullptr;
+    uint64_t *ea_mask = nullptr;
+    const size_t ne = (size_t)(n * p->R);
+    if (ix.a_i32) API_TRY(I->alloc((void **)&ea_i32, 4 * ne), "allocate edge attributes");
+    if (ix.a_f32) API_TRY(I->alloc((void **)&ea_f32, 4 * ne), "allocate edge attributes");
+    if (ix.a_mask) API_TRY(I->alloc((void **)&ea_mask, 8 * ne), "allocate edge attributes");
+    API_TRY(jag::build_edge_attrs(ix, ea_i32, ea_f32, ea_mask, 0), "edge attributes");
+    ix.ea_i32 = ea_i32; ix.ea_f32 = ea_f32; ix.ea_mask = ea_mask;
+  }
   API_TRY(cudaDeviceSynchronize(), "finish upload");
 #undef API_TRY
   *out = I;

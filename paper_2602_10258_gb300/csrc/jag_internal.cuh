@@ -49,6 +49,11 @@ struct DevIndex {
   const int32_t *si32_id;
   const float *sf32_val;
   const int32_t *sf32_id;
+  // attribute of each edge's target, laid out like the graph ([n][R]), so a
+  // hop reads neighbour ids and their attributes in one wave of loads
+  const int32_t *ea_i32;
+  const float *ea_f32;
+  const uint64_t *ea_mask;
 };
 
 // Per-query plan written by the preparation kernel.
@@ -109,31 +114,67 @@ __device__ __forceinline__ bool passes(const DevIndex &ix, int64_t u, int32_t ki
   }
 }
 
-// dist_F(a_u, f) in ordered 32-bit form (Sec. 3.1, "Examples").  lut: the
-// per-query boolean table (least flips per assignment of involved bits).
+// dist_F(a, f) in ordered 32-bit form (Sec. 3.1, "Examples") from the raw
+// attribute word a (int32 or float32 bit pattern in the low 32 bits, or the
+// 64-bit mask).  lut: the per-query boolean table (least flips per
+// assignment of the involved bits).
+__device__ __forceinline__ uint32_t filter_distance_raw(int32_t kind, uint64_t pay, const uint8_t *lut,
+                                                        uint64_t raw) {
+  // an if-chain on the (warp-uniform) kind: cheaper than a jump table
+  if (kind == JAG_F_LABEL) return (int32_t)(uint32_t)raw != lo32(pay) ? 1u : 0u;
+  if (kind == JAG_F_RANGE_I32) {
+    const int64_t a = (int32_t)(uint32_t)raw, lo = lo32(pay), hi = hi32(pay);
+    return a < lo ? (uint32_t)(lo - a) : (a > hi ? (uint32_t)(a - hi) : 0u);
+  }
+  if (kind == JAG_F_RANGE_F32) {
+    const float a = u2f((uint32_t)raw);
+    const float lo = u2f((uint32_t)lo32(pay)), hi = u2f((uint32_t)hi32(pay));
+    if (a < lo) return f2u(__fsub_rn(lo, a));
+    if (a > hi) return f2u(__fsub_rn(a, hi));
+    if (lo <= a && a <= hi) return 0u;
+    return 0x7F800000u;  // NaN bound: never satisfied
+  }
+  if (kind == JAG_F_SUBSET) return (uint32_t)__popcll(pay & ~raw);
+  if (kind == JAG_F_BOOL) return lut[compress_bits(raw, pay)];
+  if (kind == JAG_F_NONE) return 0u;
+  return 0x7F800000u;
+}
+
+// The raw attribute word a filter kind reads, for point u.
+__device__ __forceinline__ uint64_t point_attr(const DevIndex &ix, int64_t u, int32_t kind) {
+  switch (kind) {
+    case JAG_F_LABEL: case JAG_F_RANGE_I32: return (uint32_t)ix.a_i32[u];
+    case JAG_F_RANGE_F32: return f2u(ix.a_f32[u]);
+    case JAG_F_SUBSET: case JAG_F_BOOL: return ix.a_mask[u];
+    default: return 0;
+  }
+}
+
+__device__ __forceinline__ uint32_t ld_word(const void *p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_dword(const void *p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// The same word for the target of edge e (= p * R + r) from the edge table;
+// issued where it is written, next to the load of the neighbour id.
+__device__ __forceinline__ uint64_t edge_attr(const DevIndex &ix, int64_t e, int32_t kind) {
+  switch (kind) {
+    case JAG_F_LABEL: case JAG_F_RANGE_I32: return ld_word(ix.ea_i32 + e);
+    case JAG_F_RANGE_F32: return ld_word(ix.ea_f32 + e);
+    case JAG_F_SUBSET: case JAG_F_BOOL: return ld_dword(ix.ea_mask + e);
+    default: return 0;
+  }
+}
+
 __device__ __forceinline__ uint32_t filter_distance(const DevIndex &ix, int64_t u, int32_t kind,
                                                     uint64_t pay, const uint8_t *lut) {
-  switch (kind) {
-    case JAG_F_NONE: return 0u;
-    case JAG_F_LABEL: return ix.a_i32[u] != lo32(pay) ? 1u : 0u;
-    case JAG_F_RANGE_I32: {
-      int64_t a = ix.a_i32[u], lo = lo32(pay), hi = hi32(pay);
-      if (a < lo) return (uint32_t)(lo - a);
-      if (a > hi) return (uint32_t)(a - hi);
-      return 0u;
-    }
-    case JAG_F_RANGE_F32: {
-      float a = ix.a_f32[u];
-      float lo = u2f((uint32_t)lo32(pay)), hi = u2f((uint32_t)hi32(pay));
-      if (a < lo) return f2u(__fsub_rn(lo, a));
-      if (a > hi) return f2u(__fsub_rn(a, hi));
-      if (lo <= a && a <= hi) return 0u;
-      return 0x7F800000u;  // NaN bound: never satisfied
-    }
-    case JAG_F_SUBSET: return (uint32_t)__popcll(pay & ~ix.a_mask[u]);
-    case JAG_F_BOOL: return lut[compress_bits(ix.a_mask[u], pay)];
-    default: return 0x7F800000u;
-  }
+  return filter_distance_raw(kind, pay, lut, point_attr(ix, u, kind));
 }
 
 // dist_A(a_i, a_j) in ordered form (Sec. 3.1) for the build's attribute.

@@ -52,6 +52,10 @@ int list_capacity(int ls);
 // Lanes per row P and chunks per lane for a row of nchunks 16-byte chunks.
 bool row_mapping(int nchunks, int *P, int *CPL);
 
+// Fill the edge attribute tables of a finished graph (any pointer may be NULL).
+cudaError_t build_edge_attrs(const DevIndex &ix, int32_t *ea_i32, float *ea_f32, uint64_t *ea_mask,
+                             cudaStream_t stream);
+
 // GPU index build (Algorithms 3 and 4); see build.cu.
 struct BuildLaunch {
   DevIndex ix;              // graph pointer is writable

@@ -237,7 +237,7 @@ __device__ int scan_candidates(const DevIndex &ix, const float4 (&q)[CPL], const
     const bool full = cnt == k;
     const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
     const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
-    const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+    const float dist = candidate_distances<P, CPL, 8>(ix, q, S.cid, nc);
     uint64_t ck = kNoKey;
     uint32_t cv = kEmptySlot;
     if (lane < nc) {
@@ -254,7 +254,7 @@ __device__ int scan_candidates(const DevIndex &ix, const float4 (&q)[CPL], const
 // K1: each warp takes queries from a global counter and runs GreedySearch
 // with D_F (Algorithm 2) for the graph-routed ones.
 template <int CAP, int P, int CPL>
-__global__ void __launch_bounds__(kSearchWarps * 32)
+__global__ void __launch_bounds__(kSearchWarps * 32, CPL == 1 ? 8 : 1)
 query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
              const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int32_t *out_ids, float *out_dist,
              int32_t *counters, unsigned long long *work) {
@@ -407,6 +407,24 @@ merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const 
     int32_t *c = counters + qi * 4;
     c[0] = 0; c[1] = 0; c[2] = 0; c[3] = 2;
   }
+}
+
+// Edge attribute tables: the attribute of every edge's target, [n][R].
+__global__ void edge_attr_kernel(DevIndex ix, int32_t *ea_i32, float *ea_f32, uint64_t *ea_mask) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ix.n * ix.R) return;
+  const int32_t u = ix.graph[e];
+  const int64_t v = u >= 0 ? u : 0;
+  if (ea_i32) ea_i32[e] = u >= 0 ? ix.a_i32[v] : 0;
+  if (ea_f32) ea_f32[e] = u >= 0 ? ix.a_f32[v] : 0.f;
+  if (ea_mask) ea_mask[e] = u >= 0 ? ix.a_mask[v] : 0ull;
+}
+
+cudaError_t build_edge_attrs(const DevIndex &ix, int32_t *ea_i32, float *ea_f32, uint64_t *ea_mask,
+                             cudaStream_t stream) {
+  const int64_t ne = ix.n * ix.R;
+  edge_attr_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, stream>>>(ix, ea_i32, ea_f32, ea_mask);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

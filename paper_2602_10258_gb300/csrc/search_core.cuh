@@ -74,16 +74,17 @@ __device__ __forceinline__ int first_unexpanded(const uint32_t *bid, int cnt, in
   return -1;
 }
 
-// Visited-set probe; returns true if id was not recorded (new or forgotten).
+// Visited-set probe (two slots, linear); returns true if id was not
+// recorded (new, or not stored because both slots hold other ids).
 __device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t id, bool &inserted) {
   const uint32_t mask = (1u << hbits) - 1;
   const uint32_t h = (id * 0x9E3779B1u) >> (32 - hbits);
-  inserted = false;
-#pragma unroll 1
-  for (int probe = 0; probe < 8; ++probe) {
-    uint32_t slot = (h + probe) & mask;
-    uint32_t old = atomicCAS(&tab[slot], kEmptySlot, id);
-    if (old == kEmptySlot) { inserted = true; return true; }
+  uint32_t old = atomicCAS(&tab[h], kEmptySlot, id);
+  inserted = old == kEmptySlot;
+  if (old == id) return false;
+  if (!inserted) {
+    old = atomicCAS(&tab[(h + 1) & mask], kEmptySlot, id);
+    inserted = old == kEmptySlot;
     if (old == id) return false;
   }
   return true;
@@ -114,6 +115,8 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
                                                 uint32_t cv, int &r0) {
   const int lane = threadIdx.x & 31;
   bool valid = ck != kNoKey;
+  r0 = cnt;
+  if (!__any_sync(kFull, valid)) return cnt;
   const int rank = list_rank<CAP>(bkey, bid, cnt, ck, cv);
   if (valid) {
     if (rank >= ls) valid = false;
@@ -151,11 +154,11 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
 
 // Distances from the search point (lane-held chunks q) to the nc rows whose
 // ids are cid[0..nc); lane c < nc returns the distance of candidate c.
-template <int P, int CPL>
+template <int P, int CPL, int ROWS = 4>
 __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const float4 (&q)[CPL],
                                                      const uint32_t *cid, int nc) {
-  constexpr int VPW = 32 / P;                     // rows per warp-wide load
-  constexpr int U = VPW >= 4 ? 1 : 4 / VPW;       // loads in flight per lane (4 rows per warp)
+  constexpr int VPW = 32 / P;                        // rows per warp-wide load
+  constexpr int U = VPW >= ROWS ? 1 : ROWS / VPW;    // loads in flight per lane (ROWS rows per warp)
   const int lane = threadIdx.x & 31;
   const int grp = lane / P, lig = lane % P;
   float mine = 0.f;
@@ -205,22 +208,33 @@ __device__ __forceinline__ void load_point(const float *row, int d, float4 (&q)[
   }
 }
 
-// First-key policies.
+// First-key policies.  A policy with kEdgeAttr reads the neighbour's
+// attribute from the edge table in the same wave as the neighbour id.
 struct QueryKey {   // dist_F of the query's filter (Sec. 3.1)
+  static constexpr bool kEdgeAttr = true;
   int32_t kind;
   uint64_t payload;
   const uint8_t *lut;
   __device__ __forceinline__ uint32_t operator()(const DevIndex &ix, int64_t u) const {
     return filter_distance(ix, u, kind, payload, lut);
   }
+  __device__ __forceinline__ uint64_t edge_word(const DevIndex &ix, int64_t e) const {
+    return edge_attr(ix, e, kind);
+  }
+  __device__ __forceinline__ uint32_t from_word(uint64_t raw) const {
+    return filter_distance_raw(kind, payload, lut, raw);
+  }
 };
 
 struct BuildKey {   // capped dist_A from base point p with threshold t (Sec. 3.2)
+  static constexpr bool kEdgeAttr = false;   // the graph changes while it is built
   int64_t p;
   uint32_t t;
   __device__ __forceinline__ uint32_t operator()(const DevIndex &ix, int64_t u) const {
     return capped_distance(ix.dist_a, attribute_distance(ix, p, u), t);
   }
+  __device__ __forceinline__ uint64_t edge_word(const DevIndex &, int64_t) const { return 0; }
+  __device__ __forceinline__ uint32_t from_word(uint64_t) const { return 0; }
 };
 
 struct NoSink {
@@ -279,19 +293,24 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4
     int rmin = cnt;
     for (int rb = 0; rb < ix.R; rb += 32) {
       const int u = (rb + lane < ix.R) ? __ldg(row + rb + lane) : -1;
-      bool inserted = false, fresh = false;
-      if (u >= 0) fresh = visit_insert(S.hash, hbits, (uint32_t)u, inserted);
-      fill += __popc(__ballot_sync(kFull, inserted));
-      st.seen += __popc(__ballot_sync(kFull, fresh));
+      uint64_t aw = 0;
+      if (KeyFn::kEdgeAttr && u >= 0) aw = key1.edge_word(ix, (int64_t)pid * ix.R + rb + lane);
       const bool full = (cnt == ls);
       const uint64_t tkey = full ? S.bkey[ls - 1] : kNoKey;
       const uint32_t tid = full ? (S.bid[ls - 1] & ~kExpanded) : kEmptySlot;
+      // first key, and early rejection, before the visited set: a rejected
+      // neighbour is rejected again at any later meeting, so only neighbours
+      // whose distance is computed need to be remembered
       uint32_t k1 = 0;
-      bool keep = fresh;
-      if (fresh) {
-        k1 = key1(ix, u);
-        keep = !(full && k1 > (uint32_t)(tkey >> 32));
+      bool cand = u >= 0;
+      if (cand) {
+        k1 = KeyFn::kEdgeAttr ? key1.from_word(aw) : key1(ix, u);
+        cand = !(full && k1 > (uint32_t)(tkey >> 32));
       }
+      bool inserted = false, keep = false;
+      if (cand) keep = visit_insert(S.hash, hbits, (uint32_t)u, inserted);
+      fill += __popc(__ballot_sync(kFull, inserted));
+      st.seen += __popc(__ballot_sync(kFull, keep));
       const uint32_t km = __ballot_sync(kFull, keep);
       const int nc = __popc(km);
       if (keep) {
