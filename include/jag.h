@@ -161,6 +161,29 @@ JAG_API jag_status jag_search(jag_index *idx, const jag_search_args *args);
  * when the answers are in host memory.  args->stream may be NULL. */
 JAG_API jag_status jag_search_host(jag_index *idx, const jag_search_args *args);
 
+/* Search that allocates no device memory.  It does the same work, with the
+ * same arguments and answers, as jag_search, but keeps its scratch in a
+ * fixed 16 MiB area that the library reserves on every device where it is
+ * loaded (held until the process exits), so it never calls cudaMalloc or
+ * any other allocating routine.  It serves callers that cannot allocate while
+ * they search: a latency-bound serving thread must not wait for the device
+ * to drain, as cudaMalloc may; a process may have handed all device memory
+ * to its own allocator up front; some deployments forbid allocation after
+ * start-up.  The paper has no counterpart; it is a deployment option of this
+ * library.
+ *   - The first call on a device looks up the area's device address (a
+ *     one-time set-up); make that first call before any stream capture.
+ *   - Every call, on any stream, uses the same area, which keeps the
+ *     previous call's contents; calls whose device work overlaps race, so
+ *     issue them on one stream or wait for one before starting the next.
+ *   - A call that would need more scratch than 16 MiB (about 32 bytes per
+ *     query, 8 bytes per filter_aux byte, and, on indexes with a mask column
+ *     and s0 > 0, nq * scan_cap * 4 bytes) returns JAG_EINVAL with the
+ *     size it needed in jag_last_error(); split the batch, lower scan_cap,
+ *     or set s0 = 0.
+ * Other errors as jag_search. */
+JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_search_args *args);
+
 /* Index facts. */
 typedef struct jag_info {
   int64_t n, d;

@@ -169,6 +169,27 @@ jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
 
 }  // namespace
 
+namespace jag {
+
+// Read access for other translation units of the library: the device-side
+// view of an index and its device ordinal.
+bool index_view(const jag_index *idx, DevIndex *ix, int *device) {
+  if (!idx) return false;
+  *ix = idx->ix;
+  *device = idx->device;
+  return true;
+}
+
+// The argument checks of jag_search, with the thread's error message set.
+jag_status check_search(const jag_index *idx, const jag_search_args *a) {
+  g_err.clear();
+  return check_search_args(idx, a);
+}
+
+jag_status set_error(jag_status s, const char *msg) { return fail(s, "%s", msg); }
+
+}  // namespace jag
+
 extern "C" {
 
 const char *jag_last_error(void) { return g_err.c_str(); }

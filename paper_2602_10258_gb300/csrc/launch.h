@@ -52,6 +52,11 @@ int list_capacity(int ls);
 // Lanes per row P and chunks per lane for a row of nchunks 16-byte chunks.
 bool row_mapping(int nchunks, int *P, int *CPL);
 
+// Accessors of the C ABI layer for other translation units.
+bool index_view(const jag_index *idx, DevIndex *ix, int *device);
+jag_status check_search(const jag_index *idx, const jag_search_args *a);
+jag_status set_error(jag_status s, const char *msg);
+
 // Fill the edge attribute tables of a finished graph (any pointer may be NULL).
 cudaError_t build_edge_attrs(const DevIndex &ix, int32_t *ea_i32, float *ea_f32, uint64_t *ea_mask,
                              cudaStream_t stream);

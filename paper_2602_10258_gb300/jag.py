@@ -55,8 +55,8 @@ class Info(C.Structure):
                 ("n_thresholds", C.c_int32), ("dist_a", C.c_int32)]
 
 
-EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_get_info", "jag_get_graph",
-            "jag_get_thresholds", "jag_free", "jag_last_error", "jag_version"]
+EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_search_noalloc", "jag_get_info",
+            "jag_get_graph", "jag_get_thresholds", "jag_free", "jag_last_error", "jag_version"]
 
 _lib = None
 _lock = threading.Lock()
@@ -84,6 +84,8 @@ def load(build_if_missing: bool = True):
             L.jag_search.restype = C.c_int
             L.jag_search_host.argtypes = [P, C.POINTER(SearchArgs)]
             L.jag_search_host.restype = C.c_int
+            L.jag_search_noalloc.argtypes = [P, C.POINTER(SearchArgs)]
+            L.jag_search_noalloc.restype = C.c_int
             L.jag_get_info.argtypes = [P, C.POINTER(Info)]
             L.jag_get_info.restype = C.c_int
             L.jag_get_graph.argtypes = [P, P]
@@ -196,6 +198,26 @@ def jag_search(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=No
     a.ev_graph_begin = None if ev_begin is None else ev_begin.cuda_event
     a.ev_graph_end = None if ev_end is None else ev_end.cuda_event
     _check(L.jag_search(h, C.byref(a)))
+
+
+def jag_search_noalloc(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=None, stream=None,
+                       s0=-1, scan_cap=0, flags=0, hash_bits=0):
+    """jag_search without any device allocation: the library's fixed scratch
+    area is used instead (for callers that cannot allocate while searching).
+    Calls share that area, so calls whose device work overlaps race; a call
+    needing more than the area holds raises JagError (EINVAL)."""
+    import torch
+    L = load()
+    nq = queries.shape[0]
+    a = _args(nq, k, beam, s0, scan_cap, flags, hash_bits, 0 if aux is None else aux.numel())
+    a.queries = queries.data_ptr()
+    a.filters = filters.data_ptr()
+    a.filter_aux = None if aux is None or aux.numel() == 0 else aux.data_ptr()
+    a.out_ids, a.out_dist = out_ids.data_ptr(), out_dist.data_ptr()
+    a.counters = None if counters is None else counters.data_ptr()
+    st = stream if stream is not None else torch.cuda.current_stream(queries.device)
+    a.stream = st.cuda_stream
+    _check(L.jag_search_noalloc(h, C.byref(a)))
 
 
 def jag_search_host(h, queries, filters, aux, k, beam, counters=False, s0=-1, scan_cap=0, flags=0,
