@@ -369,7 +369,7 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
   int32_t ntiles;
   int64_t tile;
-  const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, cap, a->k, idx->n, scan_all, &ntiles, &tile);
+  const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, cap, a->k, idx->n, scan_all, s0, &ntiles, &tile);
   Workspace *w = idx->workspace(stream);
   std::lock_guard<std::mutex> g(w->mu);
   cudaError_t e = ensure(w->buf, L0.total, stream);
@@ -465,7 +465,7 @@ jag_status jag_search_host(jag_index *idx, const jag_search_args *a) {
     int64_t tile;
     const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, a->scan_cap <= 0 ? 8192 : a->scan_cap,
                                                              a->k, idx->n, (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0,
-                                                             &ntiles, &tile);
+                                                             a->s0 < 0 ? 2048 : a->s0, &ntiles, &tile);
     if ((e = cudaMemcpyAsync(&status, (uint8_t *)w->buf.ptr + L0.status, 4, cudaMemcpyDeviceToHost, st)))
       return cuda_fail(e, "read status");
   }

@@ -236,6 +236,20 @@ __device__ __forceinline__ float group_reduce(float acc) {
   return acc;
 }
 
+// The same butterfly for U independent accumulators, interleaved step by
+// step so that their shuffle chains overlap.
+template <int P, int U>
+__device__ __forceinline__ void group_reduce_n(float (&acc)[U]) {
+#pragma unroll
+  for (int o = P / 2; o >= 1; o >>= 1) {
+    float t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) t[u] = __shfl_xor_sync(kFull, acc[u], o);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = __fadd_rn(acc[u], t[u]);
+  }
+}
+
 // Status word bits written by kernels (read back by the host where needed).
 enum : uint32_t {
   kErrVisitedOverflow = 1u,

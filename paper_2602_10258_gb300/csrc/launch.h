@@ -30,7 +30,7 @@ struct SearchLaunch {
   int32_t *list_counts;    // [nq]
   unsigned long long *work;  // [4] work counters
   uint32_t *status;
-  uint64_t *part_key;      // brute-force partial lists [nq][ntiles][k]
+  uint64_t *part_key;      // partial top-k lists [nq][ntiles][k]
   uint32_t *part_id;
   int32_t ntiles;
   int64_t tile;
@@ -43,7 +43,11 @@ struct SearchScratch {
   size_t plans, lut, lists, list_counts, work, status, part_key, part_id, total;
 };
 SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int64_t n,
-                                    int scan_all, int32_t *ntiles, int64_t *tile);
+                                    int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile);
+// Partial top-k lists: the brute-force scan cuts the points into tiles of
+// 65536, the scan route cuts each passing set (at most max(s0, cap) ids) into
+// tiles of 1024.
+void scan_tiling(int64_t n, int scan_all, int64_t s0, int64_t cap, int32_t *ntiles, int64_t *tile);
 
 cudaError_t run_search(const SearchLaunch &L);
 

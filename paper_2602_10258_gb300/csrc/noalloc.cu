@@ -65,8 +65,9 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   const int64_t cap = a->scan_cap <= 0 ? 8192 : a->scan_cap;
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
   // scratch layout: only the regions this call can touch
-  const int64_t tile = 65536;
-  const int32_t ntiles = (int32_t)((ix.n + tile - 1) / tile);
+  int64_t tile;
+  int32_t ntiles;
+  scan_tiling(ix.n, scan_all, s0, cap, &ntiles, &tile);
   const bool lists = !scan_all && s0 > 0 && ix.a_mask != nullptr;
   size_t off = 0;
   const size_t o_plans = off; off += a256(sizeof(QueryPlan) * (size_t)(nq > 0 ? nq : 1));
@@ -75,9 +76,10 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   const size_t o_counts = off; off += a256(4 * (size_t)(nq > 0 ? nq : 1));
   const size_t o_work = off; off += 256;
   const size_t o_status = off; off += 256;
-  const size_t parts = scan_all ? (size_t)nq * (size_t)ntiles * (size_t)a->k : 1;
+  const size_t parts = (scan_all || s0 > 0) ? (size_t)nq * (size_t)ntiles * (size_t)a->k : 1;
   const size_t o_pkey = off; off += a256(parts * 8);
   const size_t o_pid = off; off += a256(parts * 4);
+  off += (!scan_all && s0 > 0) ? a256(parts * 8) : 0;   // scan work items follow the partial lists
   if (off > kNoAllocScratchBytes) {
     char msg[256];
     snprintf(msg, sizeof(msg),

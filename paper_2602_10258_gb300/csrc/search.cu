@@ -223,34 +223,6 @@ __device__ __forceinline__ void write_answers(const WarpSmem &S, int cnt, int64_
   }
 }
 
-// Exact top-k over an explicit candidate id list (all candidates pass the
-// filter), kept in the warp's list with the same merge as the search.
-template <int CAP, int P, int CPL>
-__device__ int scan_candidates(const DevIndex &ix, const float4 (&q)[CPL], const int32_t *ids, int64_t m, int k,
-                               const WarpSmem &S) {
-  const int lane = threadIdx.x & 31;
-  int cnt = 0;
-  for (int64_t b = 0; b < m; b += 32) {
-    const int nc = (int)min64(32, m - b);
-    if (lane < nc) S.cid[lane] = (uint32_t)ids[b + lane];
-    __syncwarp();
-    const bool full = cnt == k;
-    const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
-    const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
-    const float dist = candidate_distances<P, CPL, 8>(ix, q, S.cid, nc);
-    uint64_t ck = kNoKey;
-    uint32_t cv = kEmptySlot;
-    if (lane < nc) {
-      ck = make_key(0u, dist);
-      cv = S.cid[lane];
-      if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
-    }
-    int r0;
-    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
-  }
-  return cnt;
-}
-
 // K1: each warp takes queries from a global counter and runs GreedySearch
 // with D_F (Algorithm 2) for the graph-routed ones.
 template <int CAP, int P, int CPL>
@@ -285,43 +257,208 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
   }
 }
 
-// K3: exact scan of the scan-routed queries over their passing slice (label
-// and range filters) or gathered list (subset and boolean filters).
+// Rows of the nc candidates cid[0..nc) copied into shared memory with
+// asynchronous 16-byte copies, issued as one commit group (not waited for).
+__device__ __forceinline__ void stage_rows_issue(const DevIndex &ix, const uint32_t *cid, int nc, float *rows) {
+  const int lane = threadIdx.x & 31;
+  const int nch = ix.nchunks;
+  const int total = nc * nch;
+  for (int i = lane; i < total; i += 32) {
+    const int c = i / nch, ch = i - c * nch;
+    const float *src = ix.x + (int64_t)cid[c] * ix.xs + ch * 4;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(rows + (size_t)c * ix.xs + ch * 4);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Distances from the lane-held chunks q to nc rows staged in shared memory,
+// in the same lane mapping and rounding order as candidate_distances.
+template <int P, int CPL>
+__device__ __forceinline__ float staged_distances(const float4 (&q)[CPL], const float *rows, int64_t xs,
+                                                  int nchunks, int nc) {
+  constexpr int VPW = 32 / P;
+  constexpr int U = 4;   // rows reduced together
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / P, lig = lane % P;
+  float mine = 0.f;
+  for (int base = 0; base < nc; base += U * VPW) {
+    float acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = base + u * VPW + grp;
+      acc[u] = 0.f;
+      if (c < nc) {
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+          const int ch = lig + j * 32;
+          if (ch < nchunks)
+            acc[u] = chunk_accumulate(acc[u], q[j], *reinterpret_cast<const float4 *>(rows + c * xs + ch * 4));
+        }
+      }
+    }
+    group_reduce_n<P, U>(acc);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c0 = base + u * VPW;
+      const float v = __shfl_sync(kFull, acc[u], ((lane - c0) * P) & 31);
+      if (lane >= c0 && lane < c0 + VPW) mine = v;
+    }
+  }
+  return mine;
+}
+
+__device__ __forceinline__ void routed_candidates(const DevIndex &ix, const jag_filter *filters,
+                                                  const QueryPlan &pl, int64_t qi, const int32_t *lists,
+                                                  int64_t cap, const int32_t **ids, int64_t *m) {
+  if (pl.route == kRouteSlice) {
+    const int32_t kind = filters[qi].kind;
+    *ids = (kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
+    *m = pl.end - pl.begin;
+  } else {
+    *ids = lists + qi * cap;
+    *m = pl.count;
+  }
+}
+
+// K3: exact scan of the scan-routed queries.  A warp takes one tile of one
+// query's passing set (a slice of the sorted column for label and range
+// filters, the gathered list for subset and boolean ones), stages its rows
+// in shared memory round by round, and leaves the tile's top k in a partial
+// list; merge_scan_kernel combines a query's partial lists.
 template <int CAP, int P, int CPL>
 __global__ void __launch_bounds__(kSearchWarps * 32)
-scan_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
-            const int32_t *lists, int64_t cap, int64_t nq, int k, int32_t *out_ids, float *out_dist,
-            int32_t *counters, unsigned long long *work) {
+scan_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
+                 const int32_t *lists, int64_t cap, int k, int64_t tile, int ntiles, int rpr, const uint64_t *items,
+                 const unsigned long long *nitems, unsigned long long *work, uint64_t *part_key,
+                 uint32_t *part_id) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lcap = list_slots(k);
+  const size_t head = warp_smem_bytes(lcap, 5) + 32 * 4;   // list, small arrays, second id slot
+  uint8_t *wb = smem + warp * (head + 2 * (size_t)rpr * ix.xs * 4);
+  const WarpSmem S = carve_warp_smem(wb, lcap, 5);
+  uint32_t *cids[2] = {S.cid, reinterpret_cast<uint32_t *>(wb + warp_smem_bytes(lcap, 5))};
+  float *rows[2] = {reinterpret_cast<float *>(wb + head), reinterpret_cast<float *>(wb + head) + (size_t)rpr * ix.xs};
+  const unsigned long long total = *nitems;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(work, 1ull);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= total) return;
+    const uint64_t item = items[it];
+    const int64_t qi = (int64_t)(item >> 20);
+    const int t = (int)(item & 0xFFFFF);
+    const QueryPlan pl = plans[qi];
+    const int32_t *ids;
+    int64_t m;
+    routed_candidates(ix, filters, pl, qi, lists, cap, &ids, &m);
+    const int64_t b0 = (int64_t)t * tile;
+    const int64_t b1 = min64(m, b0 + tile);
+    float4 q[CPL];
+    load_point<P, CPL>(queries + qi * d, d, q);
+    int cnt = 0;
+    // round r covers [b0 + r*rpr, ...); round r+1 is in flight while r is reduced
+    const int nr = (int)((b1 - b0 + rpr - 1) / rpr);
+    {
+      const int nc0 = (int)min64(rpr, b1 - b0);
+      if (lane < nc0) cids[0][lane] = (uint32_t)ids[b0 + lane];
+      __syncwarp();
+      stage_rows_issue(ix, cids[0], nc0, rows[0]);
+    }
+    for (int r = 0; r < nr; ++r) {
+      const int cur = r & 1;
+      const int64_t b = b0 + (int64_t)r * rpr;
+      const int nc = (int)min64(rpr, b1 - b);
+      if (r + 1 < nr) {
+        const int64_t bn = b + rpr;
+        const int ncn = (int)min64(rpr, b1 - bn);
+        if (lane < ncn) cids[cur ^ 1][lane] = (uint32_t)ids[bn + lane];
+        __syncwarp();
+        stage_rows_issue(ix, cids[cur ^ 1], ncn, rows[cur ^ 1]);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncwarp();
+      const bool full = cnt == k;
+      const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
+      const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
+      const float dist = staged_distances<P, CPL>(q, rows[cur], ix.xs, ix.nchunks, nc);
+      uint64_t ck = kNoKey;
+      uint32_t cv = kEmptySlot;
+      if (lane < nc) {
+        ck = make_key(0u, dist);
+        cv = cids[cur][lane];
+        if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+      }
+      int r0;
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+      __syncwarp();   // rows[cur] and cids[cur] are reused by round r + 2
+    }
+    uint64_t *pk = part_key + (qi * ntiles + t) * k;
+    uint32_t *pi = part_id + (qi * ntiles + t) * k;
+    for (int j = lane; j < k; j += 32) {
+      pk[j] = j < cnt ? S.bkey[j] : kNoKey;
+      pi[j] = j < cnt ? S.bid[j] : kEmptySlot;
+    }
+    __syncwarp();
+  }
+}
+
+// (query, tile) work items of the scan route, compacted so that every scan
+// warp gets a real tile: items[i] = (query << 20) | tile.
+__global__ void scan_items_kernel(const DevIndex ix, const jag_filter *filters, const QueryPlan *plans,
+                                  const int32_t *lists, int64_t cap, int64_t nq, int64_t tile, uint64_t *items,
+                                  unsigned long long *nitems) {
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= nq) return;
+  const QueryPlan pl = plans[qi];
+  if (pl.route != kRouteSlice && pl.route != kRouteList) return;
+  const int32_t *ids;
+  int64_t m;
+  routed_candidates(ix, filters, pl, qi, lists, cap, &ids, &m);
+  const int64_t nt = (m + tile - 1) / tile;
+  if (nt == 0) return;
+  const unsigned long long base = atomicAdd(nitems, (unsigned long long)nt);
+  for (int64_t t = 0; t < nt; ++t) items[base + t] = ((uint64_t)qi << 20) | (uint64_t)t;
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+merge_scan_kernel(const DevIndex ix, const jag_filter *filters, const QueryPlan *plans, const int32_t *lists,
+                  int64_t cap, int64_t nq, int k, int64_t tile, int ntiles, const uint64_t *part_key,
+                  const uint32_t *part_id, int32_t *out_ids, float *out_dist, int32_t *counters) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(k);
   const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, 5), lcap, 5);
-  for (;;) {
-    unsigned long long qi = 0;
-    if (lane == 0) qi = atomicAdd(work, 1ull);
-    qi = __shfl_sync(kFull, qi, 0);
-    if (qi >= (unsigned long long)nq) return;
-    const QueryPlan pl = plans[qi];
-    if (pl.route != kRouteSlice && pl.route != kRouteList) continue;
-    float4 q[CPL];
-    load_point<P, CPL>(queries + (int64_t)qi * d, d, q);
-    const int32_t *ids;
-    int64_t m;
-    if (pl.route == kRouteSlice) {
-      const int32_t kind = filters[qi].kind;
-      ids = (kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
-      m = pl.end - pl.begin;
-    } else {
-      ids = lists + (int64_t)qi * cap;
-      m = pl.count;
+  const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + warp;
+  if (qi >= nq) return;
+  const QueryPlan pl = plans[qi];
+  if (pl.route != kRouteSlice && pl.route != kRouteList) return;
+  const int32_t *ids;
+  int64_t m;
+  routed_candidates(ix, filters, pl, qi, lists, cap, &ids, &m);
+  const int nt = (int)((m + tile - 1) / tile);
+  int cnt = 0;
+  for (int t = 0; t < nt; ++t) {
+    for (int b = 0; b < k; b += 32) {
+      uint64_t ck = kNoKey;
+      uint32_t cv = kEmptySlot;
+      if (b + lane < k) {
+        ck = part_key[(qi * ntiles + t) * k + b + lane];
+        cv = part_id[(qi * ntiles + t) * k + b + lane];
+      }
+      if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
+      int r0;
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
     }
-    const int cnt = scan_candidates<CAP, P, CPL>(ix, q, ids, m, k, S);
-    write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
-    if (counters && lane == 0) {
-      int32_t *c = counters + qi * 4;
-      c[0] = 0; c[1] = 0; c[2] = (int32_t)m; c[3] = 1;
-    }
-    __syncwarp();
+  }
+  write_answers(S, cnt, qi, k, out_ids, out_dist);
+  if (counters && lane == 0) {
+    int32_t *c = counters + qi * 4;
+    c[0] = 0; c[1] = 0; c[2] = (int32_t)m; c[3] = 1;
   }
 }
 
@@ -451,8 +588,26 @@ bool row_mapping(int nchunks, int *P, int *CPL) {
 
 static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+void scan_tiling(int64_t n, int scan_all, int64_t s0, int64_t cap, int32_t *ntiles, int64_t *tile) {
+  if (scan_all) {
+    *tile = 65536;
+    *ntiles = (int32_t)std::max<int64_t>(1, (n + *tile - 1) / *tile);
+  } else {
+    *tile = 1024;
+    const int64_t most = std::max<int64_t>(std::max<int64_t>(s0, cap), 1);
+    *ntiles = (int32_t)std::max<int64_t>(1, (most + *tile - 1) / *tile);
+  }
+}
+
+// Rows per round of the staged scan: two rounds of rows (double buffer)
+// take 16 KB of shared memory per warp.
+int scan_rows_per_round(int64_t xs) {
+  const int64_t r = 8192 / (xs * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(32, r));
+}
+
 SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int64_t n,
-                                    int scan_all, int32_t *ntiles, int64_t *tile) {
+                                    int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile) {
   SearchScratch s;
   size_t off = 0;
   s.plans = off; off += align256(sizeof(QueryPlan) * (size_t)std::max<int64_t>(nq, 1));
@@ -461,14 +616,11 @@ SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, 
   s.list_counts = off; off += align256((size_t)std::max<int64_t>(nq, 1) * 4);
   s.work = off; off += 256;
   s.status = off; off += 256;
-  int64_t t = 65536;
-  int32_t nt = (int32_t)((n + t - 1) / t);
-  if (nt < 1) nt = 1;
-  *ntiles = nt;
-  *tile = t;
-  const size_t parts = scan_all ? (size_t)std::max<int64_t>(nq, 1) * nt * k : 1;
+  scan_tiling(n, scan_all, s0, cap, ntiles, tile);
+  const size_t parts = (scan_all || s0 > 0) ? (size_t)std::max<int64_t>(nq, 1) * *ntiles * k : 1;
   s.part_key = off; off += align256(parts * 8);
   s.part_id = off; off += align256(parts * 4);
+  off += (!scan_all && s0 > 0) ? align256(parts * 8) : 0;   // scan work items, right after part_id
   s.total = off;
   return s;
 }
@@ -510,14 +662,27 @@ static cudaError_t launch_query(const SearchLaunch &L) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || L.s0 <= 0) return e;
   // the exact scan for the routed queries (k <= ls <= CAP)
-  const size_t ssm = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.k), 5);
-  auto sk = scan_kernel<CAP, P, CPL>;
+  const int rpr = scan_rows_per_round(L.ix.xs);
+  const size_t ssm = (size_t)kSearchWarps * (warp_smem_bytes(list_slots(L.k), 5) + 32 * 4 + 2 * (size_t)rpr * L.ix.xs * 4);
+  auto sk = scan_tile_kernel<CAP, P, CPL>;
+  // items live after the partial lists' id array; counters in work[2..3]
+  uint64_t *items = reinterpret_cast<uint64_t *>(L.part_id + (size_t)std::max<int64_t>(L.nq, 1) * L.ntiles * L.k);
+  items = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(items) + 255) & ~uintptr_t(255));
+  scan_items_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.ix, L.filters, L.plans, L.lists, L.cap,
+                                                                          L.nq, L.tile, items, L.work + 3);
   const int sbps = blocks_per_sm(sk, ssm);
   if (sbps == 0) return cudaErrorInvalidConfiguration;
-  const int64_t sgrid = std::min<int64_t>((int64_t)sbps * num_sms(), want);
-  sk<<<(unsigned)sgrid, kSearchWarps * 32, ssm, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lists,
-                                                           L.cap, L.nq, L.k, L.out_ids, L.out_dist, L.counters,
-                                                           L.work + 1);
+  const int64_t sgrid = std::min<int64_t>((int64_t)sbps * num_sms(),
+                                          std::max<int64_t>(1, (L.nq * L.ntiles + kSearchWarps - 1) / kSearchWarps));
+  sk<<<(unsigned)sgrid, kSearchWarps * 32, ssm, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap,
+                                                           L.k, L.tile, L.ntiles, rpr, items, L.work + 3, L.work + 2,
+                                                           L.part_key, L.part_id);
+  const size_t msm = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.k), 5);
+  auto mk = merge_scan_kernel<CAP>;
+  if (blocks_per_sm(mk, msm) == 0) return cudaErrorInvalidConfiguration;
+  mk<<<(unsigned)want, kSearchWarps * 32, msm, L.stream>>>(L.ix, L.filters, L.plans, L.lists, L.cap, L.nq, L.k,
+                                                          L.tile, L.ntiles, L.part_key, L.part_id, L.out_ids,
+                                                          L.out_dist, L.counters);
   return cudaGetLastError();
 }
 

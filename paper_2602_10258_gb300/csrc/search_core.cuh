@@ -177,17 +177,21 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const f
         }
       }
     }
+    float acc[U];
 #pragma unroll
     for (int s = 0; s < U; ++s) {
+      acc[s] = 0.f;
       if (base + s * VPW < nc) {   // warp-uniform
-        float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) acc = chunk_accumulate(acc, q[j], xv[s][j]);
-        acc = group_reduce<P>(acc);
-        const int c0 = base + s * VPW;
-        const float v = __shfl_sync(kFull, acc, ((lane - c0) * P) & 31);
-        if (lane >= c0 && lane < c0 + VPW) mine = v;
+        for (int j = 0; j < CPL; ++j) acc[s] = chunk_accumulate(acc[s], q[j], xv[s][j]);
       }
+    }
+    group_reduce_n<P, U>(acc);
+#pragma unroll
+    for (int s = 0; s < U; ++s) {
+      const int c0 = base + s * VPW;
+      const float v = __shfl_sync(kFull, acc[s], ((lane - c0) * P) & 31);
+      if (lane >= c0 && lane < c0 + VPW) mine = v;
     }
   }
   return mine;
