@@ -65,6 +65,10 @@ typedef struct {
   int32_t R;               /* out-degree bound                                  */
   int32_t *graph;          /* [n][R], -1 padded                                 */
   int64_t entry;           /* entry vertex s                                    */
+  int32_t fmt;             /* storage format of the searched rows (FMT_*)       */
+  int32_t qbytes;          /* bytes per stored row (multiple of 16)             */
+  const uint8_t *xq;       /* [n][qbytes] stored rows (BF16 / FP8), or NULL     */
+  const float *qscale;     /* [n] per-row scale of FP8 rows, or NULL            */
 } orc_index;
 
 /* ------------------------------------------------------------------------- */
@@ -117,6 +121,128 @@ double orc_dist_f64(const float *q, const float *x, int64_t d) {
     s += t * t;
   }
   return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* low-precision storage                                                      */
+/* ------------------------------------------------------------------------- */
+
+/* BF16 from fp32 by round to nearest, ties to even, on the upper 16 bits of
+ * the fp32 encoding (finite inputs). */
+uint16_t orc_bf16_encode(float x) {
+  uint32_t b = f2u(x);
+  uint32_t lsb = (b >> 16) & 1u;
+  b += 0x7FFFu + lsb;
+  return (uint16_t)(b >> 16);
+}
+float orc_bf16_decode(uint16_t h) { return u2f((uint32_t)h << 16); }
+
+/* FP8 E4M3 (OCP 8-bit floating point, E4M3): sign, 4 exponent bits with bias
+ * 7, 3 mantissa bits; exponent field 0 holds subnormals m/8 * 2^-6; the code
+ * S.1111.111 is NaN and there is no infinity, so the largest finite magnitude
+ * is 1.75 * 2^8 = 448. */
+float orc_fp8_decode(uint8_t c) {
+  int s = c >> 7, e = (c >> 3) & 15, m = c & 7;
+  float v = e == 0 ? ldexpf((float)m / 8.0f, -6) : ldexpf(1.0f + (float)m / 8.0f, e - 7);
+  return s ? -v : v;
+}
+
+/* Nearest finite E4M3 value to x, ties to the even code, magnitudes beyond the
+ * largest finite value saturating to +-448: a binary search over the 127
+ * non-negative finite codes, whose values increase with the code. */
+uint8_t orc_fp8_encode(float x) {
+  uint8_t sign = (f2u(x) >> 31) ? 0x80 : 0x00;
+  double a = fabs((double)x);
+  int lo = 0, hi = 126;                  /* codes 0..126 are finite, increasing */
+  if (a >= (double)orc_fp8_decode(126)) return sign | 126;
+  while (hi - lo > 1) {                  /* invariant: value(lo) <= a < value(hi) */
+    int mid = (lo + hi) / 2;
+    if ((double)orc_fp8_decode((uint8_t)mid) <= a) lo = mid; else hi = mid;
+  }
+  double dl = a - (double)orc_fp8_decode((uint8_t)lo), dh = (double)orc_fp8_decode((uint8_t)hi) - a;
+  int c = dl < dh ? lo : (dh < dl ? hi : ((lo & 1) ? hi : lo));
+  return sign | (uint8_t)c;
+}
+
+/* Bytes of one stored row: d elements rounded up to 16-byte chunks. */
+int orc_row_bytes(int fmt, int64_t d) {
+  int64_t eb = fmt == FMT_F32 ? 4 : (fmt == FMT_BF16 ? 2 : 1);
+  return (int)((d * eb + 15) / 16 * 16);
+}
+
+/* Quantize n fp32 rows.  BF16: each element rounded, scale 1.  FP8: scale
+ * s = max|x_i| / 448 (1 if the row is zero), codes of x_i / s (fp32
+ * divisions).  out: [n][row_bytes], zero padded. */
+void orc_quantize(const float *x, int64_t n, int64_t d, int fmt, uint8_t *out, float *scale) {
+  int rb = orc_row_bytes(fmt, d);
+  memset(out, 0, (size_t)(n * rb));
+  for (int64_t i = 0; i < n; ++i) {
+    const float *r = x + i * d;
+    uint8_t *o = out + i * rb;
+    if (fmt == FMT_BF16) {
+      for (int64_t j = 0; j < d; ++j) { uint16_t h = orc_bf16_encode(r[j]); memcpy(o + 2 * j, &h, 2); }
+      if (scale) scale[i] = 1.0f;
+    } else {
+      float mx = 0.0f;
+      for (int64_t j = 0; j < d; ++j) if (fabsf(r[j]) > mx) mx = fabsf(r[j]);
+      float s = mx > 0.0f ? mx / 448.0f : 1.0f;
+      for (int64_t j = 0; j < d; ++j) o[j] = orc_fp8_encode(r[j] / s);
+      scale[i] = s;
+    }
+  }
+}
+
+/* Element j of a stored row, as the distance uses it: s * value (fp32). */
+static inline float stored_elem(const uint8_t *row, int fmt, float s, int64_t j) {
+  if (fmt == FMT_BF16) { uint16_t h; memcpy(&h, row + 2 * j, 2); return orc_bf16_decode(h); }
+  return s * orc_fp8_decode(row[j]);
+}
+
+/* Canonical squared distance to a stored BF16 / FP8 row: the order of
+ * orc_dist_canon with 16-byte chunks of stored elements (8 BF16 or 16 FP8
+ * elements), each element decoded and scaled before t = q_i - x_i. */
+float orc_dist_canon_q(const float *q, const uint8_t *row, int fmt, float s, int64_t d) {
+  float acc[32];
+  for (int l = 0; l < 32; ++l) acc[l] = 0.0f;
+  int64_t per = fmt == FMT_BF16 ? 8 : 16;
+  int64_t nch = (d + per - 1) / per;
+  for (int64_t g = 0; g < nch; ++g) {
+    int lane = (int)(g % 32);
+    for (int64_t e = 0; e < per; ++e) {
+      int64_t i = g * per + e;
+      if (i >= d) break;
+      float t = q[i] - stored_elem(row, fmt, s, i);
+      acc[lane] = fmaf(t, t, acc[lane]);
+    }
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    float nxt[32];
+    for (int l = 0; l < 32; ++l) nxt[l] = acc[l] + acc[l ^ o];
+    memcpy(acc, nxt, sizeof(acc));
+  }
+  return acc[0];
+}
+
+/* Distance from a query to point u in the index's storage format. */
+static inline float search_dist(const orc_index *ix, const float *q, int64_t u) {
+  if (ix->fmt == FMT_F32 || !ix->xq) return orc_dist_canon(q, ix->x + u * ix->d, ix->d);
+  return orc_dist_canon_q(q, ix->xq + u * ix->qbytes, ix->fmt, ix->qscale ? ix->qscale[u] : 1.0f, ix->d);
+}
+
+void orc_bf16_encode_batch(const float *x, int64_t n, uint16_t *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_encode(x[i]);
+}
+void orc_fp8_encode_batch(const float *x, int64_t n, uint8_t *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_fp8_encode(x[i]);
+}
+void orc_fp8_decode_batch(const uint8_t *c, int64_t n, float *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_fp8_decode(c[i]);
+}
+
+void orc_dist_canon_q_batch(const float *q, const uint8_t *rows, const float *scale, int fmt, int64_t n,
+                            int64_t d, int64_t qbytes, float *out) {
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = orc_dist_canon_q(q + i * d, rows + i * qbytes, fmt, scale ? scale[i] : 1.0f, d);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -274,6 +400,13 @@ typedef struct {
   uint32_t t;
 } comparator_t;
 
+/* Vector distance of the comparator: the build compares fp32 rows; a query
+ * compares the index's stored rows (fp32, or BF16 / FP8 before re-ranking). */
+static inline float cmp_dist(const comparator_t *c, int64_t u) {
+  if (c->p >= 0) return orc_dist_canon(c->xq, c->ix->x + u * c->ix->d, c->ix->d);
+  return search_dist(c->ix, c->xq, u);
+}
+
 static inline uint32_t first_key(const comparator_t *c, int64_t u) {
   if (c->p >= 0) return orc_capped(c->ix->dist_a, orc_dist_A(c->ix, c->p, u), c->t);
   return orc_dist_F(c->ix, u, c->f, c->lut);
@@ -305,7 +438,7 @@ static void greedy_direct(const comparator_t *c, int ls, entry_t *L, int *len,
   int64_t nt = 0, nv = 0;
   int64_t s = ix->entry;
   L[0].k1 = first_key(c, s);
-  L[0].dist = orc_dist_canon(c->xq, ix->x + s * ix->d, ix->d);
+  L[0].dist = cmp_dist(c, s);
   L[0].id = (int32_t)s;
   L[0].expanded = 0;
   n = 1;
@@ -329,7 +462,7 @@ static void greedy_direct(const comparator_t *c, int ls, entry_t *L, int *len,
       cnt->seen += 1;
       uint32_t k1 = first_key(c, u);
       if (n == ls && k1 > L[n - 1].k1) continue;
-      float du = orc_dist_canon(c->xq, ix->x + u * ix->d, ix->d);
+      float du = cmp_dist(c, u);
       cnt->dc += 1;
       if (n == ls && !key_less(k1, du, (int32_t)u, L[n - 1].k1, L[n - 1].dist, L[n - 1].id)) continue;
       int pos = n < ls ? n : ls - 1;
@@ -360,7 +493,7 @@ static void greedy_literal(const comparator_t *c, int ls, int k, entry_t *out, i
   int64_t n = 0;
   int64_t s = ix->entry;
   L[n].k1 = first_key(c, s);
-  L[n].dist = orc_dist_canon(c->xq, ix->x + s * ix->d, ix->d);
+  L[n].dist = cmp_dist(c, s);
   L[n].id = (int32_t)s; L[n].expanded = 0; n++;
   *hops = 0;
   for (;;) {
@@ -384,7 +517,7 @@ static void greedy_literal(const comparator_t *c, int ls, int k, entry_t *out, i
       for (int64_t i = 0; i < n; ++i) if (L[i].id == u) { inL = 1; break; }
       if (inL) continue;
       L[n].k1 = first_key(c, u);
-      L[n].dist = orc_dist_canon(c->xq, ix->x + u * ix->d, ix->d);
+      L[n].dist = cmp_dist(c, u);
       L[n].id = (int32_t)u; L[n].expanded = 0; n++;
     }
     if (n > ls) {
@@ -552,8 +685,12 @@ static void query_range(void *ctx, int64_t lo, int64_t hi, int tid) {
   const q_ctx *c = (const q_ctx *)ctx;
   const orc_index *ix = c->ix;
   int ls = c->ls, k = c->k;
+  const int quant = ix->fmt != FMT_F32 && ix->xq;
+  /* with BF16 / FP8 storage the leading min(4k, ls) passing entries of the
+   * final list are ranked again by fp32 distance */
+  const int want = quant ? (4 * k < ls ? 4 * k : ls) : k;
   entry_t *L = (entry_t *)malloc(sizeof(entry_t) * (size_t)(ls + 1));
-  entry_t *top = (entry_t *)malloc(sizeof(entry_t) * (size_t)(k + 1));
+  entry_t *top = (entry_t *)malloc(sizeof(entry_t) * (size_t)(want + 1));
   uint8_t *seen = (uint8_t *)calloc((size_t)ix->n, 1);
   int64_t *touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)ix->n);
   for (int64_t qi = lo; qi < hi; ++qi) {
@@ -573,21 +710,25 @@ static void query_range(void *ctx, int64_t lo, int64_t hi, int tid) {
       counters_t cnt = {0, 0, 0};
       if (c->literal) {
         int64_t hops = 0;
-        greedy_literal(&cmp, ls, k, top, &m, &hops);
+        greedy_literal(&cmp, ls, want, top, &m, &hops);
         cnt.hops = hops;
       } else {
         int len = 0; int64_t nt = 0;
         greedy_direct(&cmp, ls, L, &len, seen, touched, &nt, NULL, 0, NULL, &cnt);
         for (int64_t i = 0; i < nt; ++i) seen[touched[i]] = 0;
-        m = len < k ? len : k;
+        m = len < want ? len : want;
         for (int i = 0; i < m; ++i) top[i] = L[i];
       }
-      /* Only points that pass the filter are answers. */
-      int w = 0;
-      for (int i = 0; i < m; ++i) {
-        if (top[i].k1 != 0) break;
-        oid[w] = top[i].id; od[w] = top[i].dist; ++w;
+      /* only points that pass the filter are answers (a prefix of the list) */
+      int np = 0;
+      while (np < m && top[np].k1 == 0) ++np;
+      if (quant) {
+        for (int i = 0; i < np; ++i)
+          top[i].dist = orc_dist_canon(c->q + qi * ix->d, ix->x + (int64_t)top[i].id * ix->d, ix->d);
+        qsort(top, (size_t)np, sizeof(entry_t), entry_cmp);
       }
+      int w = 0;
+      for (int i = 0; i < np && w < k; ++i) { oid[w] = top[i].id; od[w] = top[i].dist; ++w; }
       for (; w < k; ++w) { oid[w] = -1; od[w] = INFINITY; }
       if (cn) { cn[0] = cnt.hops; cn[1] = cnt.seen; cn[2] = cnt.dc; cn[3] = 0; }
     }

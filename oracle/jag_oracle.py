@@ -37,11 +37,15 @@ def compile_lib(force: bool = False) -> str:
     return _LIB
 
 
+FMT_F32, FMT_BF16, FMT_FP8 = 0, 1, 2
+
+
 class _Index(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("x", C.c_void_p),
                 ("a_i32", C.c_void_p), ("a_f32", C.c_void_p), ("a_mask", C.c_void_p),
                 ("dist_a", C.c_int32), ("R", C.c_int32), ("graph", C.c_void_p),
-                ("entry", C.c_int64)]
+                ("entry", C.c_int64), ("fmt", C.c_int32), ("qbytes", C.c_int32),
+                ("xq", C.c_void_p), ("qscale", C.c_void_p)]
 
 
 def lib():
@@ -70,6 +74,12 @@ def lib():
                 "orc_count_passing": (I64, [P, P, P]),
                 "orc_dist_A": (C.c_uint32, [P, I64, I64]),
                 "orc_capped": (C.c_uint32, [I32, C.c_uint32, C.c_uint32]),
+                "orc_row_bytes": (I32, [I32, I64]),
+                "orc_quantize": (None, [P, I64, I64, I32, P, P]),
+                "orc_bf16_encode_batch": (None, [P, I64, P]),
+                "orc_fp8_encode_batch": (None, [P, I64, P]),
+                "orc_fp8_decode_batch": (None, [P, I64, P]),
+                "orc_dist_canon_q_batch": (None, [P, P, P, I32, I64, I64, I64, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -98,7 +108,7 @@ class Index:
     """Base vectors, attributes and (optionally) a graph, as the oracle sees them."""
 
     def __init__(self, x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=K_RANGE_I32,
-                 R=32, graph=None, entry=0):
+                 R=32, graph=None, entry=0, storage=FMT_F32):
         self.x = _c(x, np.float32)
         self.attr_i32 = _c(attr_i32, np.int32)
         self.attr_f32 = _c(attr_f32, np.float32)
@@ -107,12 +117,17 @@ class Index:
         self.R = int(R)
         self.graph = (np.full((n, self.R), -1, np.int32) if graph is None
                       else np.ascontiguousarray(graph, dtype=np.int32))
+        self.xq, self.qscale, qb = None, None, 0
+        if storage != FMT_F32:
+            self.xq, self.qscale = quantize(self.x, storage)
+            qb = self.xq.shape[1]
         self.s = _Index(n, d, _p(self.x), _p(self.attr_i32), _p(self.attr_f32),
-                        _p(self.attr_mask), int(dist_a), self.R, _p(self.graph), int(entry))
+                        _p(self.attr_mask), int(dist_a), self.R, _p(self.graph), int(entry),
+                        int(storage), qb, _p(self.xq), _p(self.qscale))
 
     @classmethod
-    def from_workload(cls, w, R=32, graph=None, entry=0):
-        return cls(w.x, w.attr_i32, w.attr_f32, w.attr_mask, w.dist_a, R, graph, entry)
+    def from_workload(cls, w, R=32, graph=None, entry=0, storage=FMT_F32):
+        return cls(w.x, w.attr_i32, w.attr_f32, w.attr_mask, w.dist_a, R, graph, entry, storage)
 
     @property
     def n(self):
@@ -295,3 +310,50 @@ def dist_A(ix: Index, i, j):
 
 def capped(dist_a, da, t):
     return int(lib().orc_capped(int(dist_a), int(da), int(t)))
+
+
+def row_bytes(fmt, d):
+    return int(lib().orc_row_bytes(int(fmt), int(d)))
+
+
+def quantize(x, fmt):
+    """Stored rows [n][row_bytes] (uint8) and per-row scales of BF16 / FP8
+    storage, from the format definitions."""
+    x = _c(x, np.float32)
+    n, d = x.shape
+    rb = row_bytes(fmt, d)
+    out = np.empty((n, rb), np.uint8)
+    scale = np.empty(n, np.float32)
+    lib().orc_quantize(_p(x), n, d, int(fmt), _p(out), _p(scale))
+    return out, scale
+
+
+def bf16_encode(x):
+    x = _c(np.atleast_1d(x), np.float32)
+    out = np.empty(x.shape, np.uint16)
+    lib().orc_bf16_encode_batch(_p(x), x.size, _p(out))
+    return out
+
+
+def fp8_encode(x):
+    x = _c(np.atleast_1d(x), np.float32)
+    out = np.empty(x.shape, np.uint8)
+    lib().orc_fp8_encode_batch(_p(x), x.size, _p(out))
+    return out
+
+
+def fp8_decode(c):
+    c = _c(np.atleast_1d(c), np.uint8)
+    out = np.empty(c.shape, np.float32)
+    lib().orc_fp8_decode_batch(_p(c), c.size, _p(out))
+    return out
+
+
+def dist_canon_q_rows(q, rows, scale, fmt):
+    q = _c(np.atleast_2d(q), np.float32)
+    rows = _c(np.atleast_2d(rows), np.uint8)
+    scale = _c(scale, np.float32)
+    out = np.empty(q.shape[0], np.float32)
+    lib().orc_dist_canon_q_batch(_p(q), _p(rows), _p(scale), int(fmt), q.shape[0], q.shape[1], rows.shape[1],
+                                 _p(out))
+    return out
