@@ -203,6 +203,13 @@ JAG_API jag_status jag_get_graph(const jag_index *idx, int32_t *host_out);
  * JAG_EINVAL if the graph was uploaded rather than built. */
 JAG_API jag_status jag_get_thresholds(const jag_index *idx, uint32_t *host_out);
 
+/* Copy the stored BF16 / FP8 rows [n][row_bytes] (row_bytes = d * element
+ * bytes rounded up to 16; zero padded) and the per-row scales [n] to host
+ * memory (the paper stores fp32 vectors; this is the low-precision storage option).
+ * row_bytes_out receives row_bytes.  JAG_EINVAL for an fp32 index. */
+JAG_API jag_status jag_get_stored_rows(const jag_index *idx, uint8_t *rows_out, float *scales_out,
+                                       int32_t *row_bytes_out);
+
 /* Release the index and its device memory.  NULL is allowed. */
 JAG_API void jag_free(jag_index *idx);
 

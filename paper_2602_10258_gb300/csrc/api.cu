@@ -204,7 +204,8 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
   if (p->d < 1 || p->d > 1024) return fail(JAG_EINVAL, "d must be in [1, 1024]");
   if (!p->x) return fail(JAG_EINVAL, "x is NULL");
   if (p->R < 1 || p->R > 64) return fail(JAG_EINVAL, "R must be in [1, 64]");
-  if (p->storage != JAG_VEC_F32) return fail(JAG_EUNSUPPORTED, "storage format not available in this build");
+  if (p->storage != JAG_VEC_F32 && p->storage != JAG_VEC_BF16 && p->storage != JAG_VEC_FP8)
+    return fail(JAG_EINVAL, "bad storage format");
   const bool prebuilt = p->graph != nullptr;
   if (!prebuilt) {
     if (p->l_b < 1 || p->l_b > 256) return fail(JAG_EINVAL, "l_b must be in [1, 256]");
@@ -256,6 +257,19 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
   API_TRY(cudaMemcpy2D(I->x, sizeof(float) * xs, p->x, sizeof(float) * d, sizeof(float) * d, (size_t)n,
                        cudaMemcpyHostToDevice), "copy vectors");
   ix.x = I->x;
+  ix.fmt = p->storage;
+  if (p->storage != JAG_VEC_F32) {
+    const int64_t eb = p->storage == JAG_VEC_BF16 ? 2 : 1;
+    ix.qbytes = (int32_t)((d * eb + 15) / 16 * 16);
+    ix.qchunks = ix.qbytes / 16;
+    uint8_t *xq;
+    float *qs;
+    API_TRY(I->alloc((void **)&xq, (size_t)(n * ix.qbytes)), "allocate stored rows");
+    API_TRY(I->alloc((void **)&qs, sizeof(float) * (size_t)n), "allocate row scales");
+    API_TRY(jag::quantize_rows(ix, p->storage, xq, qs, 0), "quantize rows");
+    ix.xq = xq;
+    ix.qscale = qs;
+  }
   if (p->attr_i32) {
     int32_t *a, *sv, *si;
     API_TRY(I->alloc((void **)&a, 4 * (size_t)n), "allocate attr_i32");
@@ -362,6 +376,18 @@ jag_status jag_get_thresholds(const jag_index *idx, uint32_t *host_out) {
   return e == cudaSuccess ? JAG_OK : cuda_fail(e, "copy thresholds");
 }
 
+jag_status jag_get_stored_rows(const jag_index *idx, uint8_t *rows_out, float *scales_out, int32_t *row_bytes_out) {
+  if (!idx) return fail(JAG_EINVAL, "NULL index");
+  if (idx->ix.fmt == JAG_VEC_F32) return fail(JAG_EINVAL, "index stores fp32 rows");
+  if (row_bytes_out) *row_bytes_out = idx->ix.qbytes;
+  DeviceGuard dg(idx->device);
+  cudaError_t e = cudaSuccess;
+  if (rows_out) e = cudaMemcpy(rows_out, idx->ix.xq, (size_t)(idx->n * idx->ix.qbytes), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && scales_out)
+    e = cudaMemcpy(scales_out, idx->ix.qscale, sizeof(float) * (size_t)idx->n, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? JAG_OK : cuda_fail(e, "copy stored rows");
+}
+
 static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream_t stream) {
   const int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
   const int64_t s0 = a->s0 < 0 ? 2048 : a->s0;
@@ -369,7 +395,8 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
   int32_t ntiles;
   int64_t tile;
-  const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, cap, a->k, idx->n, scan_all, s0, &ntiles, &tile);
+  const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, cap, a->k, a->beam, idx->n, idx->ix.fmt,
+                                                           scan_all, s0, &ntiles, &tile);
   Workspace *w = idx->workspace(stream);
   std::lock_guard<std::mutex> g(w->mu);
   cudaError_t e = ensure(w->buf, L0.total, stream);
@@ -395,6 +422,8 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   L.part_key = (uint64_t *)(base + L0.part_key);
   L.part_id = (uint32_t *)(base + L0.part_id);
   L.ntiles = ntiles; L.tile = tile;
+  L.rr = L0.rr;
+  L.rr_ids = (int32_t *)(base + L0.rr_ids);
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
   L.ev_end = (cudaEvent_t)a->ev_graph_end;
   L.stream = stream;
@@ -464,7 +493,8 @@ jag_status jag_search_host(jag_index *idx, const jag_search_args *a) {
     int32_t ntiles;
     int64_t tile;
     const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, a->scan_cap <= 0 ? 8192 : a->scan_cap,
-                                                             a->k, idx->n, (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0,
+                                                             a->k, a->beam, idx->n, idx->ix.fmt,
+                                                             (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0,
                                                              a->s0 < 0 ? 2048 : a->s0, &ntiles, &tile);
     if ((e = cudaMemcpyAsync(&status, (uint8_t *)w->buf.ptr + L0.status, 4, cudaMemcpyDeviceToHost, st)))
       return cuda_fail(e, "read status");

@@ -173,12 +173,12 @@ build_search_kernel(DevIndex ix, int64_t pos0, int64_t nb, int nT, const uint32_
     const int64_t bi = (int64_t)(it / nT);
     const int ti = (int)(it % nT);
     const int64_t p = order_id(pos0 + bi, ix.entry);
-    float4 q[CPL];
+    QChunks<CPL, JAG_VEC_F32> q;
     load_point<P, CPL>(ix.x + p * ix.xs, (int)ix.xs, q);
     const BuildKey key{p, thr[p * nT + ti]};
     VisitSink sink{vis_ids + it * vcap, vis_d + it * vcap, vcap, 0};
     SearchStats st;
-    greedy_search<CAP, P, CPL>(ix, key, q, lb, hbits, S, sink, st);
+    greedy_search<CAP, P, CPL, JAG_VEC_F32>(ix, key, q, lb, hbits, S, sink, st);
     if (lane == 0) {
       vis_n[it] = sink.n;
       if (sink.n > vcap) atomicOr(status, kErrVisitedOverflow);
@@ -266,7 +266,7 @@ __device__ void joint_prune(const DevIndex &ix, int64_t p, const PruneSmem &S, i
       const float dpv = u2f((uint32_t)S.skey[i]);
       bool keep = true;
       if (!in_list(S.chosen, nchosen, v) && nb > 0) {
-        float4 xv[CPL];
+        QChunks<CPL, JAG_VEC_F32> xv;
         load_point<P, CPL>(ix.x + (int64_t)v * ix.xs, (int)ix.xs, xv);
         for (int b0 = 0; b0 < nb && keep; b0 += 32) {
           const int m = min(32, nb - b0);
@@ -431,7 +431,7 @@ edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, cons
       const int nc = deg + ns;
       for (int j = lane; j < nc; j += 32) S.cid[j] = j < deg ? (uint32_t)row[j] : (uint32_t)src[j - deg];
       __syncwarp();
-      float4 xv[CPL];
+      QChunks<CPL, JAG_VEC_F32> xv;
       load_point<P, CPL>(ix.x + (int64_t)v * ix.xs, (int)ix.xs, xv);
       for (int b = 0; b < nc; b += 32) {
         const int m = min(32, nc - b);

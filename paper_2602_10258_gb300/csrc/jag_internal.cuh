@@ -17,6 +17,8 @@
 // like the value.  (first, distance bits) form one 64-bit key.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,6 +56,21 @@ struct DevIndex {
   const int32_t *ea_i32;
   const float *ea_f32;
   const uint64_t *ea_mask;
+  // rows in the storage format the search reads (BF16 / FP8); fp32 rows (x)
+  // stay for the build, the exact scan and the fp32 re-rank
+  const uint8_t *xq;
+  const float *qscale;      // per-row scale of FP8 rows
+  int32_t fmt;              // jag_vec_format
+  int32_t qbytes;           // bytes per stored row (multiple of 16)
+  int32_t qchunks;          // 16-byte chunks per stored row
+  int32_t pad1;
+};
+
+// Elements of one 16-byte chunk of a stored row, per format.
+template <int FMT>
+struct RowFmt {
+  static constexpr int E = FMT == JAG_VEC_F32 ? 4 : (FMT == JAG_VEC_BF16 ? 8 : 16);
+  static constexpr int Q4 = E / 4;   // float4 registers of query per chunk
 };
 
 // Per-query plan written by the preparation kernel.
@@ -226,6 +243,55 @@ __device__ __forceinline__ float chunk_accumulate(float acc, float4 q, float4 x)
   t = __fsub_rn(q.z, x.z); acc = __fmaf_rn(t, t, acc);
   t = __fsub_rn(q.w, x.w); acc = __fmaf_rn(t, t, acc);
   return acc;
+}
+
+__device__ __forceinline__ uint4 ld_chunk_u4(const void *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ float acc_elem(float acc, float q, float x) {
+  const float t = __fsub_rn(q, x);
+  return __fmaf_rn(t, t, acc);
+}
+
+// One 16-byte chunk of a stored row in format FMT: elements in increasing
+// order, each as acc = fma(t, t, acc), t = q_i - x_i; BF16 elements are exact
+// in fp32; FP8 elements are decoded exactly and multiplied by the row's
+// scale s (rounded to fp32) first.
+template <int FMT>
+__device__ __forceinline__ float chunk_acc(float acc, const float4 (&q)[RowFmt<FMT>::Q4], uint4 raw, float s) {
+  if constexpr (FMT == JAG_VEC_F32) {
+    return chunk_accumulate(acc, q[0], make_float4(u2f(raw.x), u2f(raw.y), u2f(raw.z), u2f(raw.w)));
+  } else if constexpr (FMT == JAG_VEC_BF16) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 qq = q[i >> 1];
+      const float q0 = (i & 1) ? qq.z : qq.x, q1 = (i & 1) ? qq.w : qq.y;
+      acc = acc_elem(acc, q0, u2f(w[i] << 16));
+      acc = acc_elem(acc, q1, u2f(w[i] & 0xFFFF0000u));
+    }
+    return acc;
+  } else {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
+      const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+      const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+      const float4 qq = q[i];
+      acc = acc_elem(acc, qq.x, __fmul_rn(s, a.x));
+      acc = acc_elem(acc, qq.y, __fmul_rn(s, a.y));
+      acc = acc_elem(acc, qq.z, __fmul_rn(s, b.x));
+      acc = acc_elem(acc, qq.w, __fmul_rn(s, b.y));
+    }
+    return acc;
+  }
 }
 
 // Butterfly over the P lanes of a group: acc_l + acc_(l xor o), o = P/2..1.

@@ -34,16 +34,25 @@ struct SearchLaunch {
   uint32_t *part_id;
   int32_t ntiles;
   int64_t tile;
+  int32_t rr;              // re-ranked candidates per query (BF16 / FP8 rows)
+  int32_t *rr_ids;         // [nq][rr]
   cudaEvent_t ev_begin, ev_end;
   cudaStream_t stream;
 };
 
+// Graph-search launch for rows stored in format FMT (search_<fmt>.cu).
+template <int FMT>
+cudaError_t launch_graph_fmt(const SearchLaunch &L);
+
 // Scratch layout of a search; sizes in bytes, offsets 256-aligned.
 struct SearchScratch {
-  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, total;
+  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, rr_ids, total;
+  int32_t rr;
 };
-SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int64_t n,
-                                    int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile);
+SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int32_t ls, int64_t n,
+                                    int fmt, int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile);
+// Candidates re-ranked in fp32 per query with BF16 / FP8 rows: min(4k, ls).
+inline int32_t rerank_count(int32_t k, int32_t ls) { return 4 * k < ls ? 4 * k : ls; }
 // Partial top-k lists: the brute-force scan cuts the points into tiles of
 // 65536, the scan route cuts each passing set (at most max(s0, cap) ids) into
 // tiles of 1024.
@@ -55,6 +64,9 @@ cudaError_t run_search(const SearchLaunch &L);
 int list_capacity(int ls);
 // Lanes per row P and chunks per lane for a row of nchunks 16-byte chunks.
 bool row_mapping(int nchunks, int *P, int *CPL);
+
+// BF16 / FP8 rows of an index from its fp32 rows (quant.cu).
+cudaError_t quantize_rows(const DevIndex &ix, int fmt, uint8_t *xq, float *qscale, cudaStream_t stream);
 
 // Accessors of the C ABI layer for other translation units.
 bool index_view(const jag_index *idx, DevIndex *ix, int *device);

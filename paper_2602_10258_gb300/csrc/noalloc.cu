@@ -80,6 +80,8 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   const size_t o_pkey = off; off += a256(parts * 8);
   const size_t o_pid = off; off += a256(parts * 4);
   off += (!scan_all && s0 > 0) ? a256(parts * 8) : 0;   // scan work items follow the partial lists
+  const int32_t rr = ix.fmt != JAG_VEC_F32 ? rerank_count(a->k, a->beam) : 0;
+  const size_t o_rr = off; off += a256((size_t)(nq > 0 ? nq : 1) * (size_t)(rr > 0 ? rr : 1) * 4);
   if (off > kNoAllocScratchBytes) {
     char msg[256];
     snprintf(msg, sizeof(msg),
@@ -119,6 +121,8 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   L.part_key = (uint64_t *)(base + o_pkey);
   L.part_id = (uint32_t *)(base + o_pid);
   L.ntiles = ntiles; L.tile = tile;
+  L.rr = rr;
+  L.rr_ids = (int32_t *)(base + o_rr);
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
   L.ev_end = (cudaEvent_t)a->ev_graph_end;
   L.stream = stream;

@@ -1,0 +1,102 @@
+// K1: the graph-search kernel of a query batch, for rows stored in format FMT
+// (one translation unit per format keeps compile units small).
+#pragma once
+
+#include <algorithm>
+
+#include "launch.h"
+#include "launch_util.cuh"
+#include "search_core.cuh"
+
+namespace jag {
+
+// Each warp takes queries from a global counter and runs GreedySearch with
+// D_F (Algorithm 2) for the graph-routed ones.  With fp32 rows it writes the
+// answers; with BF16 / FP8 rows it leaves the ids of the leading rr passing
+// entries of the final list for the fp32 re-rank.
+template <int CAP, int P, int CPL, int FMT>
+__global__ void __launch_bounds__(kSearchWarps * 32, CPL == 1 ? 8 : 1)
+query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
+             const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int rr, int32_t *rr_ids,
+             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lcap = list_slots(ls);
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, hbits), lcap, hbits);
+  for (;;) {
+    unsigned long long qi = 0;
+    if (lane == 0) qi = atomicAdd(work, 1ull);
+    qi = __shfl_sync(kFull, qi, 0);
+    if (qi >= (unsigned long long)nq) return;
+    const QueryPlan pl = plans[qi];
+    if (pl.route != kRouteGraph) continue;
+    QChunks<CPL, FMT> q;
+    load_point<P, CPL, FMT>(queries + (int64_t)qi * d, d, q);
+    const jag_filter f = filters[qi];
+    const QueryKey key{f.kind, f.payload, pl.lut_off >= 0 ? lut_base + pl.lut_off : nullptr};
+    NoSink sink;
+    SearchStats st;
+    const int cnt = greedy_search<CAP, P, CPL, FMT>(ix, key, q, ls, hbits, S, sink, st);
+    if (FMT == JAG_VEC_F32) {
+      write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
+    } else {
+      for (int j = lane; j < rr; j += 32) {
+        int32_t id = -1;
+        if (j < cnt && (S.bkey[j] >> 32) == 0) id = (int32_t)(S.bid[j] & ~kExpanded);
+        rr_ids[(int64_t)qi * rr + j] = id;
+      }
+    }
+    if (counters && lane == 0) {
+      int32_t *c = counters + qi * 4;
+      c[0] = st.hops; c[1] = st.seen; c[2] = st.dcs; c[3] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+template <int CAP, int P, int CPL, int FMT>
+static cudaError_t launch_graph_one(const SearchLaunch &L) {
+  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.ls), L.hbits);
+  auto kern = query_kernel<CAP, P, CPL, FMT>;
+  const int bps = blocks_per_sm(kern, smem);
+  if (bps == 0) return cudaErrorInvalidConfiguration;
+  const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
+  const int64_t grid = std::min<int64_t>((int64_t)bps * num_sms(), want);
+  if (L.ev_begin) cudaEventRecord(L.ev_begin, L.stream);
+  kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lut,
+                                                             L.nq, L.k, L.ls, L.hbits, L.rr, L.rr_ids, L.out_ids,
+                                                             L.out_dist, L.counters, L.work);
+  if (L.ev_end) cudaEventRecord(L.ev_end, L.stream);
+  return cudaGetLastError();
+}
+
+template <int CAP, int FMT>
+static cudaError_t launch_graph_cap(const SearchLaunch &L, int P, int CPL) {
+#define JAG_GCASE(PP, CC) \
+  if (P == PP && CPL == CC) return launch_graph_one<CAP, PP, CC, FMT>(L);
+  JAG_GCASE(8, 1)
+  JAG_GCASE(16, 1)
+  JAG_GCASE(32, 1)
+  JAG_GCASE(32, 2)
+  JAG_GCASE(32, 4)
+  if constexpr (FMT == JAG_VEC_F32) {
+    JAG_GCASE(32, 8)
+  }
+#undef JAG_GCASE
+  return cudaErrorInvalidValue;
+}
+
+template <int FMT>
+cudaError_t launch_graph_fmt(const SearchLaunch &L) {
+  int P, CPL;
+  const int nch = FMT == JAG_VEC_F32 ? L.ix.nchunks : L.ix.qchunks;
+  if (!row_mapping(nch, &P, &CPL)) return cudaErrorInvalidValue;
+  switch (list_capacity(L.ls)) {
+    case 64: return launch_graph_cap<64, FMT>(L, P, CPL);
+    case 128: return launch_graph_cap<128, FMT>(L, P, CPL);
+    case 256: return launch_graph_cap<256, FMT>(L, P, CPL);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace jag

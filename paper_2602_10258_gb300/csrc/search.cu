@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "launch.h"
+#include "launch_util.cuh"
 #include "search_core.cuh"
 
 namespace jag {
@@ -208,55 +209,6 @@ __global__ void finalize_routes_kernel(QueryPlan *plans, const int32_t *counts, 
   if (c > cap) plans[qi].route = kRouteGraph;
 }
 
-__device__ __forceinline__ void write_answers(const WarpSmem &S, int cnt, int64_t qi, int k, int32_t *out_ids,
-                                              float *out_dist) {
-  const int lane = threadIdx.x & 31;
-  for (int j = lane; j < k; j += 32) {
-    int32_t id = -1;
-    float dd = __int_as_float(0x7F800000);
-    if (j < cnt) {
-      const uint64_t kk = S.bkey[j];
-      if ((kk >> 32) == 0) { id = (int32_t)(S.bid[j] & ~kExpanded); dd = u2f((uint32_t)kk); }
-    }
-    out_ids[qi * k + j] = id;
-    out_dist[qi * k + j] = dd;
-  }
-}
-
-// K1: each warp takes queries from a global counter and runs GreedySearch
-// with D_F (Algorithm 2) for the graph-routed ones.
-template <int CAP, int P, int CPL>
-__global__ void __launch_bounds__(kSearchWarps * 32, CPL == 1 ? 8 : 1)
-query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
-             const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int32_t *out_ids, float *out_dist,
-             int32_t *counters, unsigned long long *work) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lcap = list_slots(ls);
-  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, hbits), lcap, hbits);
-  for (;;) {
-    unsigned long long qi = 0;
-    if (lane == 0) qi = atomicAdd(work, 1ull);
-    qi = __shfl_sync(kFull, qi, 0);
-    if (qi >= (unsigned long long)nq) return;
-    const QueryPlan pl = plans[qi];
-    if (pl.route != kRouteGraph) continue;
-    float4 q[CPL];
-    load_point<P, CPL>(queries + (int64_t)qi * d, d, q);
-    const jag_filter f = filters[qi];
-    const QueryKey key{f.kind, f.payload, pl.lut_off >= 0 ? lut_base + pl.lut_off : nullptr};
-    NoSink sink;
-    SearchStats st;
-    const int cnt = greedy_search<CAP, P, CPL>(ix, key, q, ls, hbits, S, sink, st);
-    write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
-    if (counters && lane == 0) {
-      int32_t *c = counters + qi * 4;
-      c[0] = st.hops; c[1] = st.seen; c[2] = st.dcs; c[3] = 0;
-    }
-    __syncwarp();
-  }
-}
-
 // Rows of the nc candidates cid[0..nc) copied into shared memory with
 // asynchronous 16-byte copies, issued as one commit group (not waited for).
 __device__ __forceinline__ void stage_rows_issue(const DevIndex &ix, const uint32_t *cid, int nc, float *rows) {
@@ -275,7 +227,7 @@ __device__ __forceinline__ void stage_rows_issue(const DevIndex &ix, const uint3
 // Distances from the lane-held chunks q to nc rows staged in shared memory,
 // in the same lane mapping and rounding order as candidate_distances.
 template <int P, int CPL>
-__device__ __forceinline__ float staged_distances(const float4 (&q)[CPL], const float *rows, int64_t xs,
+__device__ __forceinline__ float staged_distances(const QChunks<CPL, JAG_VEC_F32> &q, const float *rows, int64_t xs,
                                                   int nchunks, int nc) {
   constexpr int VPW = 32 / P;
   constexpr int U = 4;   // rows reduced together
@@ -293,7 +245,7 @@ __device__ __forceinline__ float staged_distances(const float4 (&q)[CPL], const 
         for (int j = 0; j < CPL; ++j) {
           const int ch = lig + j * 32;
           if (ch < nchunks)
-            acc[u] = chunk_accumulate(acc[u], q[j], *reinterpret_cast<const float4 *>(rows + c * xs + ch * 4));
+            acc[u] = chunk_accumulate(acc[u], q.v[j][0], *reinterpret_cast<const float4 *>(rows + c * xs + ch * 4));
         }
       }
     }
@@ -355,7 +307,7 @@ scan_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
     routed_candidates(ix, filters, pl, qi, lists, cap, &ids, &m);
     const int64_t b0 = (int64_t)t * tile;
     const int64_t b1 = min64(m, b0 + tile);
-    float4 q[CPL];
+    QChunks<CPL, JAG_VEC_F32> q;
     load_point<P, CPL>(queries + qi * d, d, q);
     int cnt = 0;
     // round r covers [b0 + r*rpr, ...); round r+1 is in flight while r is reduced
@@ -483,7 +435,7 @@ brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fi
   }
   const jag_filter f = filters[qi];
   const uint8_t *tt = f.kind == JAG_F_BOOL ? aux + f.aux_off : nullptr;
-  float4 q[CPL];
+  QChunks<CPL, JAG_VEC_F32> q;
   load_point<P, CPL>(queries + qi * d, d, q);
   const int64_t b0 = (int64_t)t * tile, b1 = min64(ix.n, b0 + tile);
   int cnt = 0;
@@ -546,6 +498,47 @@ merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const 
   }
 }
 
+// K5: fp32 re-rank for BF16 / FP8 storage.  The graph kernel leaves the ids
+// of the leading rr passing entries of each final list (-1 padded); their
+// canonical fp32 distances are computed from the fp32 rows and the best k,
+// by (distance, id), are the answers.
+template <int CAP, int P, int CPL>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+rerank_kernel(DevIndex ix, const float *queries, int d, const QueryPlan *plans, int64_t nq, int k, int rr,
+              const int32_t *rr_ids, int32_t *out_ids, float *out_dist) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lcap = list_slots(k);
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, 5), lcap, 5);
+  const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + warp;
+  if (qi >= nq) return;
+  if (plans[qi].route != kRouteGraph) return;
+  QChunks<CPL, JAG_VEC_F32> q;
+  load_point<P, CPL>(queries + qi * d, d, q);
+  int cnt = 0;
+  for (int b = 0; b < rr; b += 32) {
+    const int32_t id = b + lane < rr ? rr_ids[qi * rr + b + lane] : -1;
+    const int nc = __popc(__ballot_sync(kFull, id >= 0));   // valid ids form a prefix
+    if (nc == 0) break;
+    if (lane < nc) S.cid[lane] = (uint32_t)id;
+    __syncwarp();
+    const bool full = cnt == k;
+    const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
+    const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
+    const float dist = candidate_distances<P, CPL, 4, JAG_VEC_F32>(ix, q, S.cid, nc);
+    uint64_t ck = kNoKey;
+    uint32_t cv = kEmptySlot;
+    if (lane < nc) {
+      ck = make_key(0u, dist);
+      cv = S.cid[lane];
+      if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+    }
+    int r0;
+    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+  }
+  write_answers(S, cnt, qi, k, out_ids, out_dist);
+}
+
 // Edge attribute tables: the attribute of every edge's target, [n][R].
 __global__ void edge_attr_kernel(DevIndex ix, int32_t *ea_i32, float *ea_f32, uint64_t *ea_mask) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -606,8 +599,8 @@ int scan_rows_per_round(int64_t xs) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(32, r));
 }
 
-SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int64_t n,
-                                    int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile) {
+SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int32_t ls, int64_t n,
+                                    int fmt, int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile) {
   SearchScratch s;
   size_t off = 0;
   s.plans = off; off += align256(sizeof(QueryPlan) * (size_t)std::max<int64_t>(nq, 1));
@@ -621,46 +614,15 @@ SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, 
   s.part_key = off; off += align256(parts * 8);
   s.part_id = off; off += align256(parts * 4);
   off += (!scan_all && s0 > 0) ? align256(parts * 8) : 0;   // scan work items, right after part_id
+  s.rr = fmt != JAG_VEC_F32 ? rerank_count(k, ls) : 0;
+  s.rr_ids = off; off += align256((size_t)std::max<int64_t>(nq, 1) * std::max(s.rr, 1) * 4);
   s.total = off;
   return s;
 }
 
-template <class Kern>
-static int blocks_per_sm(Kern kern, size_t smem) {
-  static std::mutex mu;
-  std::lock_guard<std::mutex> g(mu);
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kSearchWarps * 32, smem) != cudaSuccess) b = 1;
-  return b > 0 ? b : 0;
-}
-
-static int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
 template <int CAP, int P, int CPL>
-static cudaError_t launch_query(const SearchLaunch &L) {
-  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.ls), L.hbits);
-  auto kern = query_kernel<CAP, P, CPL>;
-  const int bps = blocks_per_sm(kern, smem);
-  if (bps == 0) return cudaErrorInvalidConfiguration;
+static cudaError_t launch_scan(const SearchLaunch &L) {
   const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
-  const int64_t grid = std::min<int64_t>((int64_t)bps * num_sms(), want);
-  if (L.ev_begin) cudaEventRecord(L.ev_begin, L.stream);
-  kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lut,
-                                                             L.nq, L.k, L.ls, L.hbits, L.out_ids, L.out_dist,
-                                                             L.counters, L.work);
-  if (L.ev_end) cudaEventRecord(L.ev_end, L.stream);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || L.s0 <= 0) return e;
   // the exact scan for the routed queries (k <= ls <= CAP)
   const int rpr = scan_rows_per_round(L.ix.xs);
   const size_t ssm = (size_t)kSearchWarps * (warp_smem_bytes(list_slots(L.k), 5) + 32 * 4 + 2 * (size_t)rpr * L.ix.xs * 4);
@@ -687,6 +649,17 @@ static cudaError_t launch_query(const SearchLaunch &L) {
 }
 
 template <int CAP, int P, int CPL>
+static cudaError_t launch_rerank(const SearchLaunch &L) {
+  const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
+  const size_t sm = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.k), 5);
+  auto rk = rerank_kernel<CAP, P, CPL>;
+  if (blocks_per_sm(rk, sm) == 0) return cudaErrorInvalidConfiguration;
+  rk<<<(unsigned)want, kSearchWarps * 32, sm, L.stream>>>(L.ix, L.queries, L.d, L.plans, L.nq, L.k, L.rr, L.rr_ids,
+                                                         L.out_ids, L.out_dist);
+  return cudaGetLastError();
+}
+
+template <int CAP, int P, int CPL>
 static cudaError_t launch_brute(const SearchLaunch &L) {
   const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(CAP, 5);
   auto kern = brute_tile_kernel<CAP, P, CPL>;
@@ -701,10 +674,16 @@ static cudaError_t launch_brute(const SearchLaunch &L) {
   return cudaGetLastError();
 }
 
+enum Job { kJobScan, kJobBrute, kJobRerank };
+
 template <int CAP>
-static cudaError_t dispatch_rows(const SearchLaunch &L, int P, int CPL, bool brute) {
-#define JAG_CASE(PP, CC)                                                          \
-  if (P == PP && CPL == CC) return brute ? launch_brute<CAP, PP, CC>(L) : launch_query<CAP, PP, CC>(L);
+static cudaError_t dispatch_rows(const SearchLaunch &L, int P, int CPL, Job job) {
+#define JAG_CASE(PP, CC)                                                    \
+  if (P == PP && CPL == CC) {                                               \
+    if (job == kJobBrute) return launch_brute<CAP, PP, CC>(L);              \
+    if (job == kJobRerank) return launch_rerank<CAP, PP, CC>(L);            \
+    return launch_scan<CAP, PP, CC>(L);                                     \
+  }
   JAG_CASE(8, 1)
   JAG_CASE(16, 1)
   JAG_CASE(32, 1)
@@ -713,6 +692,15 @@ static cudaError_t dispatch_rows(const SearchLaunch &L, int P, int CPL, bool bru
   JAG_CASE(32, 8)
 #undef JAG_CASE
   return cudaErrorInvalidValue;
+}
+
+static cudaError_t dispatch_job(const SearchLaunch &L, int P, int CPL, Job job, int cap_of) {
+  switch (list_capacity(cap_of)) {
+    case 64: return dispatch_rows<64>(L, P, CPL, job);
+    case 128: return dispatch_rows<128>(L, P, CPL, job);
+    case 256: return dispatch_rows<256>(L, P, CPL, job);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t run_search(const SearchLaunch &L) {
@@ -728,15 +716,7 @@ cudaError_t run_search(const SearchLaunch &L) {
         L.out_ids, L.out_dist, L.counters, L.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (L.scan_all) {
-    const int cap = list_capacity(L.k);
-    switch (cap) {
-      case 64: return dispatch_rows<64>(L, P, CPL, true);
-      case 128: return dispatch_rows<128>(L, P, CPL, true);
-      case 256: return dispatch_rows<256>(L, P, CPL, true);
-      default: return cudaErrorInvalidValue;
-    }
-  }
+  if (L.scan_all) return dispatch_job(L, P, CPL, kJobBrute, L.k);
   if (L.s0 > 0 && L.ix.a_mask) {
     dim3 grid((unsigned)((L.ix.n + kGatherTile - 1) / kGatherTile), (unsigned)((L.nq + kGatherQPB - 1) / kGatherQPB));
     gather_list_kernel<<<grid, 256, 0, L.stream>>>(L.ix, L.filters, L.aux, L.plans, L.nq, L.cap, L.lists,
@@ -745,12 +725,18 @@ cudaError_t run_search(const SearchLaunch &L) {
                                                                                  L.cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  switch (list_capacity(L.ls)) {
-    case 64: return dispatch_rows<64>(L, P, CPL, false);
-    case 128: return dispatch_rows<128>(L, P, CPL, false);
-    case 256: return dispatch_rows<256>(L, P, CPL, false);
+  // graph search in the stored format, then the fp32 re-rank when the rows
+  // are BF16 / FP8, then the exact scan of the routed queries
+  switch (L.ix.fmt) {
+    case JAG_VEC_F32: e = launch_graph_fmt<JAG_VEC_F32>(L); break;
+    case JAG_VEC_BF16: e = launch_graph_fmt<JAG_VEC_BF16>(L); break;
+    case JAG_VEC_FP8: e = launch_graph_fmt<JAG_VEC_FP8>(L); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
+  if (L.ix.fmt != JAG_VEC_F32 && (e = dispatch_job(L, P, CPL, kJobRerank, L.k)) != cudaSuccess) return e;
+  if (L.s0 > 0) return dispatch_job(L, P, CPL, kJobScan, L.k);
+  return cudaSuccess;
 }
 
 }  // namespace jag

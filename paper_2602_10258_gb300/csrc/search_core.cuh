@@ -152,28 +152,42 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
   return n2 < ls ? n2 : ls;
 }
 
+// The lane-held chunks of a search point: lane lig of a P-lane group holds
+// chunks lig, lig + 32, ... (at most CPL of them), each as E/4 float4.
+template <int CPL, int FMT>
+struct QChunks {
+  float4 v[CPL][RowFmt<FMT>::Q4];
+};
+
 // Distances from the search point (lane-held chunks q) to the nc rows whose
-// ids are cid[0..nc); lane c < nc returns the distance of candidate c.
-template <int P, int CPL, int ROWS = 4>
-__device__ __forceinline__ float candidate_distances(const DevIndex &ix, const float4 (&q)[CPL],
+// ids are cid[0..nc), rows stored in format FMT; lane c < nc returns the
+// distance of candidate c.
+template <int P, int CPL, int ROWS = 4, int FMT = JAG_VEC_F32>
+__device__ __forceinline__ float candidate_distances(const DevIndex &ix, const QChunks<CPL, FMT> &q,
                                                      const uint32_t *cid, int nc) {
   constexpr int VPW = 32 / P;                        // rows per warp-wide load
   constexpr int U = VPW >= ROWS ? 1 : ROWS / VPW;    // loads in flight per lane (ROWS rows per warp)
   const int lane = threadIdx.x & 31;
   const int grp = lane / P, lig = lane % P;
+  const int nch = FMT == JAG_VEC_F32 ? ix.nchunks : ix.qchunks;
   float mine = 0.f;
   for (int base = 0; base < nc; base += VPW * U) {
-    float4 xv[U][CPL];
+    uint4 xv[U][CPL];
+    float sc[U];
 #pragma unroll
     for (int s = 0; s < U; ++s) {
+      sc[s] = 1.f;
       if (base + s * VPW < nc) {   // warp-uniform
         const int c = base + s * VPW + grp;
         const bool ok = c < nc;
-        const float *row = ix.x + (int64_t)(ok ? cid[c] : 0u) * ix.xs;
+        const uint32_t id = ok ? cid[c] : 0u;
+        const uint8_t *row = FMT == JAG_VEC_F32 ? reinterpret_cast<const uint8_t *>(ix.x + (int64_t)id * ix.xs)
+                                                : ix.xq + (int64_t)id * ix.qbytes;
+        if (FMT == JAG_VEC_FP8) sc[s] = ok ? __ldg(ix.qscale + id) : 1.f;
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
           const int ch = lig + j * 32;
-          xv[s][j] = (ok && ch < ix.nchunks) ? ld_chunk(row + ch * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+          xv[s][j] = (ok && ch < nch) ? ld_chunk_u4(row + ch * 16) : make_uint4(0, 0, 0, 0);
         }
       }
     }
@@ -183,7 +197,7 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const f
       acc[s] = 0.f;
       if (base + s * VPW < nc) {   // warp-uniform
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) acc[s] = chunk_accumulate(acc[s], q[j], xv[s][j]);
+        for (int j = 0; j < CPL; ++j) acc[s] = chunk_acc<FMT>(acc[s], q.v[j], xv[s][j], sc[s]);
       }
     }
     group_reduce_n<P, U>(acc);
@@ -199,16 +213,21 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const f
 
 // Lane chunks of a search point given as a contiguous fp32 row of d values
 // (not necessarily 16-byte aligned); elements past d are zero.
-template <int P, int CPL>
-__device__ __forceinline__ void load_point(const float *row, int d, float4 (&q)[CPL]) {
+template <int P, int CPL, int FMT = JAG_VEC_F32>
+__device__ __forceinline__ void load_point(const float *row, int d, QChunks<CPL, FMT> &q) {
+  constexpr int E = RowFmt<FMT>::E;
   const int lig = (threadIdx.x & 31) % P;
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    const int e = (lig + j * 32) * 4;
-    q[j].x = e + 0 < d ? row[e + 0] : 0.f;
-    q[j].y = e + 1 < d ? row[e + 1] : 0.f;
-    q[j].z = e + 2 < d ? row[e + 2] : 0.f;
-    q[j].w = e + 3 < d ? row[e + 3] : 0.f;
+    const int e0 = (lig + j * 32) * E;
+#pragma unroll
+    for (int i = 0; i < RowFmt<FMT>::Q4; ++i) {
+      const int e = e0 + 4 * i;
+      q.v[j][i].x = e + 0 < d ? row[e + 0] : 0.f;
+      q.v[j][i].y = e + 1 < d ? row[e + 1] : 0.f;
+      q.v[j][i].z = e + 2 < d ? row[e + 2] : 0.f;
+      q.v[j][i].w = e + 3 < d ? row[e + 3] : 0.f;
+    }
   }
 }
 
@@ -264,8 +283,8 @@ struct SearchStats {
 
 // Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
 // hold the final list L (count returned).
-template <int CAP, int P, int CPL, class KeyFn, class Sink>
-__device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4 (&q)[CPL], int ls,
+template <int CAP, int P, int CPL, int FMT, class KeyFn, class Sink>
+__device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunks<CPL, FMT> &q, int ls,
                              int hbits, const WarpSmem &S, Sink &sink, SearchStats &st) {
   const int lane = threadIdx.x & 31;
   const uint32_t hsize = 1u << hbits;
@@ -276,7 +295,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4
   if (lane == 0) { S.cid[0] = (uint32_t)s; S.hash[((uint32_t)s * 0x9E3779B1u) >> (32 - hbits)] = (uint32_t)s; }
   __syncwarp();
   {
-    const float d0 = candidate_distances<P, CPL>(ix, q, S.cid, 1);
+    const float d0 = candidate_distances<P, CPL, 4, FMT>(ix, q, S.cid, 1);
     const uint32_t k0 = key1(ix, s);
     const float d0b = __shfl_sync(kFull, d0, 0);
     if (lane == 0) { S.bkey[0] = make_key(k0, d0b); S.bid[0] = (uint32_t)s; }
@@ -325,7 +344,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4
       __syncwarp();
       if (nc == 0) continue;
       st.dcs += nc;
-      const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+      const float dist = candidate_distances<P, CPL, 4, FMT>(ix, q, S.cid, nc);
       uint64_t ck = kNoKey;
       uint32_t cv = kEmptySlot;
       if (lane < nc) {
@@ -346,6 +365,21 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const float4
     }
   }
   return cnt;
+}
+
+__device__ __forceinline__ void write_answers(const WarpSmem &S, int cnt, int64_t qi, int k, int32_t *out_ids,
+                                              float *out_dist) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < k; j += 32) {
+    int32_t id = -1;
+    float dd = __int_as_float(0x7F800000);
+    if (j < cnt) {
+      const uint64_t kk = S.bkey[j];
+      if ((kk >> 32) == 0) { id = (int32_t)(S.bid[j] & ~kExpanded); dd = u2f((uint32_t)kk); }
+    }
+    out_ids[qi * k + j] = id;
+    out_dist[qi * k + j] = dd;
+  }
 }
 
 }  // namespace jag

@@ -56,7 +56,8 @@ class Info(C.Structure):
 
 
 EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_search_noalloc", "jag_get_info",
-            "jag_get_graph", "jag_get_thresholds", "jag_free", "jag_last_error", "jag_version"]
+            "jag_get_graph", "jag_get_thresholds", "jag_get_stored_rows", "jag_free", "jag_last_error",
+            "jag_version"]
 
 _lib = None
 _lock = threading.Lock()
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = True):
             L.jag_get_graph.restype = C.c_int
             L.jag_get_thresholds.argtypes = [P, P]
             L.jag_get_thresholds.restype = C.c_int
+            L.jag_get_stored_rows.argtypes = [P, P, P, C.POINTER(C.c_int32)]
+            L.jag_get_stored_rows.restype = C.c_int
             L.jag_free.argtypes = [P]
             L.jag_free.restype = None
             L.jag_last_error.argtypes = []
@@ -168,6 +171,17 @@ def jag_get_thresholds(h) -> np.ndarray:
     out = np.empty((info["n"], info["n_thresholds"]), np.uint32)
     _check(load().jag_get_thresholds(h, _np_ptr(out)))
     return out
+
+
+def jag_get_stored_rows(h):
+    """(rows [n][row_bytes] uint8, scales [n] float32) of a BF16 / FP8 index."""
+    info = jag_get_info(h)
+    rb = C.c_int32(0)
+    _check(load().jag_get_stored_rows(h, None, None, C.byref(rb)))
+    rows = np.empty((info["n"], rb.value), np.uint8)
+    sc = np.empty(info["n"], np.float32)
+    _check(load().jag_get_stored_rows(h, _np_ptr(rows), _np_ptr(sc), C.byref(rb)))
+    return rows, sc
 
 
 def _args(nq, k, beam, s0, scan_cap, flags, hash_bits, aux_bytes):
@@ -276,6 +290,9 @@ class Index:
 
     def thresholds(self):
         return jag_get_thresholds(self.h)
+
+    def stored_rows(self):
+        return jag_get_stored_rows(self.h)
 
     def search(self, queries, filters, aux, k, beam, counters=False, stream=None, s0=-1, scan_cap=0,
                flags=0, hash_bits=0, ev_begin=None, ev_end=None):
