@@ -322,6 +322,20 @@ def run_ours(args):
     e2e_rec = recall_at_k(pin_ids.numpy(), gt_ids, gt_d)
     assert np.array_equal(pin_ids.numpy(), ids.cpu().numpy())
 
+    # the same graph with BF16 / FP8 rows (searched in that format, fp32
+    # re-rank of the top min(4k, beam)), swept and timed the same way
+    graph_host, entry = idx.graph(), info["entry"]
+    forms = {}
+    for fname, fcode in (("bf16", jag.JAG_VEC_BF16), ("fp8", jag.JAG_VEC_FP8)):
+        fidx = jag.Index.from_workload(w, R=R, graph=graph_host, entry=entry, storage=fcode, device=local)
+        forms[fname] = measure_form(jag, fidx, q, ft, at, nq, band, gt_ids, gt_d, min(args.steps, 100), flush,
+                                    stream)
+        forms[fname]["distance_error_vs_fp64"] = stored_distance_error(fidx, w, gt_ids, fcode)
+        fidx.close()
+        log("%s: beam %s, %.0f QPS" % (fname, forms[fname]["beam"], forms[fname]["qps"]))
+    forms["fp32"] = {"beam": chosen, "qps": round(value / world, 1), "recall": sweep[chosen],
+                     "graph_kernel_ms": round(float(kern_ms.mean()), 3)}
+
     cpu, ocnt = None, None
     if rank == 0 and not args.no_cpu:
         cpu, ocnt = cpu_baseline(w, idx, chosen, gt_ids, gt_d, budget_s=args.cpu_seconds)
@@ -367,6 +381,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(nq * K * 8),
                 "recall": float(np.nanmean(e2e_rec))},
         "cpu_baseline": cpu,
+        "forms": forms,
         "clocks": clk.summary(),
         "gpu_launches": int(args.steps * 3),
     }
@@ -375,6 +390,73 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     idx.close()
+
+
+def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stream):
+    """Smallest beam of the ladder with recall@10 >= 0.95 in every band, and
+    the device time of a whole-batch search at that beam."""
+    import torch
+    dev = q.device
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    chosen, per = None, None
+    for beam in BEAMS:
+        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy(), gt_ids, gt_d)
+        per = {}
+        for j, (_, _, name) in enumerate(BANDS):
+            m = (band == j) & ~np.isnan(rec)
+            if m.any():
+                per[name] = float(np.mean(rec[m]))
+        if all(v >= 0.95 for v in per.values()):
+            chosen = beam
+            break
+    if chosen is None:
+        chosen = BEAMS[-1]
+    for _ in range(3):
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0)
+    ts, ks = [], []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ka.record(stream)
+        kb.record(stream)
+        a.record(stream)
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, ev_begin=ka, ev_end=kb)
+        b.record(stream)
+        ts.append((a, b, ka, kb))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b, _, _ in ts]))
+    kms = float(np.mean([ka.elapsed_time(kb) for _, _, ka, kb in ts]))
+    return {"beam": chosen, "qps": round(nq / (ms / 1000.0), 1), "ms_per_step": round(ms, 4),
+            "graph_kernel_ms": round(kms, 3), "recall": per, "steps": steps}
+
+
+def stored_distance_error(idx, w, gt_ids, fcode, pairs=2000):
+    """Relative error of the squared distance to the stored (dequantized)
+    row against the fp64 distance to the fp32 row, over answer pairs."""
+    rows, sc = idx.stored_rows()
+    d = w.d
+    rng = np.random.default_rng(0)
+    qi = rng.integers(0, len(w.q), pairs)
+    pi = gt_ids[qi, 0]
+    ok = pi >= 0
+    qi, pi = qi[ok], pi[ok]
+    r = rows[pi]
+    if fcode == 1:   # BF16: the upper half of an fp32 encoding
+        xq = (r[:, :2 * d].copy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    else:            # FP8 E4M3: sign, 4-bit exponent (bias 7), 3-bit mantissa, times the row scale
+        c = r[:, :d].astype(np.int64)
+        e, m = (c >> 3) & 15, c & 7
+        mag = np.where(e == 0, m / 8.0 * 2.0 ** -6, (1 + m / 8.0) * 2.0 ** (e - 7))
+        xq = np.where(c >> 7, -mag, mag) * sc[pi][:, None].astype(np.float64)
+    qq = w.q[qi].astype(np.float64)
+    exact = ((qq - w.x[pi].astype(np.float64)) ** 2).sum(1)
+    approx = ((qq - xq) ** 2).sum(1)
+    rel = np.abs(approx - exact) / np.maximum(exact, 1e-30)
+    return {"pairs": int(len(qi)), "max_rel": float(rel.max()), "mean_rel": float(rel.mean())}
 
 
 def cpu_baseline(w, idx, beam, gt_ids, gt_d, budget_s=15.0):

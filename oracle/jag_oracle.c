@@ -479,6 +479,168 @@ static void greedy_direct(const comparator_t *c, int ls, entry_t *L, int *len,
   *ntouched = nt;
 }
 
+/* ------------------------------------------------------------------------- */
+/* learned beam width and stop hop (a search policy on top of Algorithm 1)   */
+/* ------------------------------------------------------------------------- */
+
+enum { POL_PLAIN = 0, POL_LEARNED = 1, POL_FORCED = 2 };
+#define NFEAT 12
+#define HID 64
+
+typedef struct {
+  int32_t mode;             /* POL_*                                            */
+  int32_t h0;               /* hops at the fixed beam before the decision       */
+  const uint16_t *w_bf16;   /* W1 [64][12], W2 [64][64], W3 [nl+1][64], BF16    */
+  const float *b_f32;       /* b1 [64], b2 [64], b3 [nl+1]                       */
+  float tau;                /* least margin between the two largest beam logits */
+  float stop_scale;         /* stop hop = rint(output * stop_scale)             */
+  int32_t n_ladder;         /* beam classes (nl <= 16)                          */
+  int32_t ladder[16];       /* beam of each class                               */
+  const int32_t *forced;    /* [nq][2] (beam, stop) for POL_FORCED              */
+  float *features;          /* [nq][12] out, or NULL                            */
+  int32_t *decisions;       /* [nq][4] out: beam, stop, last top-k change, learned */
+} orc_policy;
+
+/* Network output for feature vector x: two hidden layers of 64 ReLU units and
+ * nl + 1 outputs; weights in BF16, fp32 accumulation acc = fma(w, x_i, acc)
+ * over the inputs in order, starting from the bias. */
+void orc_mlp_infer(const orc_policy *pol, const float *x, float *out) {
+  const uint16_t *w1 = pol->w_bf16, *w2 = w1 + HID * NFEAT, *w3 = w2 + HID * HID;
+  const float *b1 = pol->b_f32, *b2 = b1 + HID, *b3 = b2 + HID;
+  float h1[HID], h2[HID];
+  for (int j = 0; j < HID; ++j) {
+    float acc = b1[j];
+    for (int i = 0; i < NFEAT; ++i) acc = fmaf(orc_bf16_decode(w1[j * NFEAT + i]), x[i], acc);
+    h1[j] = acc > 0.0f ? acc : 0.0f;
+  }
+  for (int j = 0; j < HID; ++j) {
+    float acc = b2[j];
+    for (int i = 0; i < HID; ++i) acc = fmaf(orc_bf16_decode(w2[j * HID + i]), h1[i], acc);
+    h2[j] = acc > 0.0f ? acc : 0.0f;
+  }
+  for (int o = 0; o <= pol->n_ladder; ++o) {
+    float acc = b3[o];
+    for (int i = 0; i < HID; ++i) acc = fmaf(orc_bf16_decode(w3[o * HID + i]), h2[i], acc);
+    out[o] = acc;
+  }
+}
+
+/* Monotone stand-in for log2 of a non-negative float from its encoding:
+ * (bits >> 16) / 128 - 127, exact in fp32. */
+static inline float flog(float x) { return (float)(f2u(x) >> 16) * 0.0078125f - 127.0f; }
+
+/* Features of the search state after the decision hop: selectivity bucket,
+ * filter kind, fraction of L passing, distances of the best, k-th passing
+ * (or last) and last entries, answers found, expanded prefix of L. */
+static void policy_features(const entry_t *L, int n, int k, int64_t est, int kind, float *f) {
+  int np = 0;
+  while (np < n && L[np].k1 == 0) ++np;
+  int fu = n;
+  for (int i = 0; i < n; ++i) if (!L[i].expanded) { fu = i; break; }
+  uint32_t e = est > 0x7FFFFFFE ? 0x7FFFFFFFu : (uint32_t)est + 1u;
+  f[0] = (float)(32 - __builtin_clz(e)) * 0.05f;
+  for (int i = 0; i < 5; ++i) f[1 + i] = (kind == i + 1) ? 1.0f : 0.0f;
+  f[6] = (float)np / (float)n;
+  f[7] = flog(L[0].dist) * 0.125f;
+  f[8] = flog(np > 0 ? L[(np < k ? np : k) - 1].dist : L[n - 1].dist) * 0.125f;
+  f[9] = (float)(np < k ? np : k) / (float)k;
+  f[10] = (float)fu / (float)n;
+  f[11] = flog(L[n - 1].dist) * 0.125f;
+}
+
+/* Beam and stop hop from the network: the largest beam logit wins (lowest
+ * class on a tie); if it leads the runner-up by less than tau the fixed beam
+ * is kept and no stop hop is set. */
+static void policy_decide(const orc_policy *pol, const float *f, int fixed, int h0, int *beam, int *stop,
+                          int *learned) {
+  float out[17];
+  orc_mlp_infer(pol, f, out);
+  int nl = pol->n_ladder, c = 0;
+  for (int i = 1; i < nl; ++i) if (out[i] > out[c]) c = i;
+  float second = -INFINITY;
+  for (int i = 0; i < nl; ++i) if (i != c && out[i] > second) second = out[i];
+  float margin = out[c] - second;
+  if (!(margin >= pol->tau)) { *beam = fixed; *stop = 0; *learned = 0; return; }
+  float r = rintf(out[nl] * pol->stop_scale);
+  int st;
+  if (!(r == r) || r >= 65535.0f) st = 65535;
+  else if (r <= (float)h0) st = h0;
+  else st = (int)r;
+  *beam = pol->ladder[c]; *stop = st; *learned = 1;
+}
+
+/* The direct search (as greedy_direct) run in two phases: h0 hops at the
+ * fixed beam ls0, then the beam and stop hop of the policy (L is cut to the
+ * new beam if longer; the search also ends once stop hops are done).  Tracks
+ * the last hop that inserted an entry among the first k. */
+static void greedy_policy(const comparator_t *c, int ls0, int k, const orc_policy *pol, const int32_t *forced_q,
+                          int64_t est, int kind, entry_t *L, int *len, uint8_t *seen, int64_t *touched,
+                          int64_t *ntouched, counters_t *cnt, float *feat, int32_t *dec) {
+  const orc_index *ix = c->ix;
+  int n = 0, ls = ls0;
+  int64_t nt = 0;
+  int stop = 0, learned = 0, decided = 0;
+  int64_t last_change = 0;
+  int64_t s = ix->entry;
+  L[0].k1 = first_key(c, s);
+  L[0].dist = cmp_dist(c, s);
+  L[0].id = (int32_t)s;
+  L[0].expanded = 0;
+  n = 1;
+  seen[s] = 1; touched[nt++] = s;
+  cnt->dc += 1;
+  if (feat) for (int i = 0; i < NFEAT; ++i) feat[i] = 0.0f;
+  for (;;) {
+    if (stop > 0 && cnt->hops >= stop) break;
+    int sel = -1;
+    for (int i = 0; i < n; ++i) if (!L[i].expanded) { sel = i; break; }
+    if (sel < 0) break;
+    L[sel].expanded = 1;
+    cnt->hops += 1;
+    int64_t p = L[sel].id;
+    const int32_t *row = ix->graph + p * ix->R;
+    for (int r = 0; r < ix->R; ++r) {
+      int64_t u = row[r];
+      if (u < 0) continue;
+      if (seen[u]) continue;
+      seen[u] = 1; touched[nt++] = u;
+      cnt->seen += 1;
+      uint32_t k1 = first_key(c, u);
+      if (n == ls && k1 > L[n - 1].k1) continue;
+      float du = cmp_dist(c, u);
+      cnt->dc += 1;
+      if (n == ls && !key_less(k1, du, (int32_t)u, L[n - 1].k1, L[n - 1].dist, L[n - 1].id)) continue;
+      int pos = n < ls ? n : ls - 1;
+      while (pos > 0 && key_less(k1, du, (int32_t)u, L[pos - 1].k1, L[pos - 1].dist, L[pos - 1].id)) {
+        L[pos] = L[pos - 1];
+        --pos;
+      }
+      L[pos].k1 = k1; L[pos].dist = du; L[pos].id = (int32_t)u; L[pos].expanded = 0;
+      if (n < ls) ++n;
+      if (pos < k) last_change = cnt->hops;
+    }
+    if (!decided && pol->mode != POL_PLAIN && cnt->hops == pol->h0) {
+      float f[NFEAT];
+      policy_features(L, n, k, est, kind, f);
+      if (feat) memcpy(feat, f, sizeof(f));
+      int beam = ls;
+      if (pol->mode == POL_LEARNED) {
+        policy_decide(pol, f, ls0, pol->h0, &beam, &stop, &learned);
+      } else {
+        beam = forced_q[0] > 0 ? forced_q[0] : ls0;
+        stop = forced_q[1] > 0 ? (forced_q[1] < pol->h0 ? pol->h0 : forced_q[1]) : 0;
+        learned = forced_q[0] > 0;
+      }
+      ls = beam;
+      if (n > ls) n = ls;
+      decided = 1;
+    }
+  }
+  *len = n;
+  *ntouched = nt;
+  if (dec) { dec[0] = ls; dec[1] = stop; dec[2] = (int32_t)last_change; dec[3] = learned; }
+}
+
 /* Literal form, for checking the direct one: L and V are plain sets; each
  * iteration takes the best unexpanded member of L, adds every out-neighbour
  * not already in L, and if L grew beyond ls re-ranks it and keeps the best
@@ -678,7 +840,20 @@ typedef struct {
   int k, ls, literal;
   int64_t s0, scan_cap;
   int32_t *ids; float *dist; int64_t *counters; /* [nq][4]: hops, seen, dc, routed */
+  const orc_policy *pol;                        /* NULL: plain search          */
 } q_ctx;
+
+/* Passing-count estimate the policy sees: exact for label / range filters,
+ * sample hits * N / S for subset / boolean ones (the routing estimator). */
+static int64_t policy_estimate(const orc_index *ix, const orc_filter *f, const uint8_t *aux) {
+  if (f->kind == K_SUBSET || f->kind == K_BOOL) {
+    int64_t S = ix->n < 4096 ? ix->n : 4096, hits = 0;
+    for (int64_t j = 0; j < S; ++j) hits += orc_g(ix, j * ix->n / S, f, aux);
+    return hits * ix->n / S;
+  }
+  if (f->kind == K_NONE) return ix->n;
+  return orc_count_passing(ix, f, aux);
+}
 
 static void query_range(void *ctx, int64_t lo, int64_t hi, int tid) {
   (void)tid;
@@ -689,7 +864,7 @@ static void query_range(void *ctx, int64_t lo, int64_t hi, int tid) {
   /* with BF16 / FP8 storage the leading min(4k, ls) passing entries of the
    * final list are ranked again by fp32 distance */
   const int want = quant ? (4 * k < ls ? 4 * k : ls) : k;
-  entry_t *L = (entry_t *)malloc(sizeof(entry_t) * (size_t)(ls + 1));
+  entry_t *L = (entry_t *)malloc(sizeof(entry_t) * (size_t)((ls > 256 ? ls : 256) + 1));
   entry_t *top = (entry_t *)malloc(sizeof(entry_t) * (size_t)(want + 1));
   uint8_t *seen = (uint8_t *)calloc((size_t)ix->n, 1);
   int64_t *touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)ix->n);
@@ -708,7 +883,16 @@ static void query_range(void *ctx, int64_t lo, int64_t hi, int tid) {
       comparator_t cmp = {ix, c->q + qi * ix->d, f, lut, -1, 0};
       int m = 0;
       counters_t cnt = {0, 0, 0};
-      if (c->literal) {
+      if (c->pol) {
+        int len = 0; int64_t nt = 0;
+        const int32_t *fq = c->pol->forced ? c->pol->forced + qi * 2 : NULL;
+        greedy_policy(&cmp, ls, k, c->pol, fq, policy_estimate(ix, f, c->aux), f->kind, L, &len, seen, touched,
+                      &nt, &cnt, c->pol->features ? c->pol->features + qi * NFEAT : NULL,
+                      c->pol->decisions ? c->pol->decisions + qi * 4 : NULL);
+        for (int64_t i = 0; i < nt; ++i) seen[touched[i]] = 0;
+        m = len < want ? len : want;
+        for (int i = 0; i < m; ++i) top[i] = L[i];
+      } else if (c->literal) {
         int64_t hops = 0;
         greedy_literal(&cmp, ls, want, top, &m, &hops);
         cnt.hops = hops;
@@ -743,9 +927,23 @@ int orc_query(const orc_index *ix, const float *q, const orc_filter *f, const ui
               int64_t nq, int k, int ls, int literal, int64_t s0, int64_t scan_cap,
               int32_t *ids, float *dist, int64_t *counters, int nthreads) {
   if (k < 1 || ls < k) return 1;
-  q_ctx c = {ix, q, f, aux, k, ls, literal, s0, scan_cap, ids, dist, counters};
+  q_ctx c = {ix, q, f, aux, k, ls, literal, s0, scan_cap, ids, dist, counters, NULL};
   parallel_for(nq, nthreads, query_range, &c);
   return 0;
+}
+
+/* Query with a search policy (learned or forced beam and stop hop). */
+int orc_query_policy(const orc_index *ix, const float *q, const orc_filter *f, const uint8_t *aux,
+                     int64_t nq, int k, int ls, int64_t s0, int64_t scan_cap, const orc_policy *pol,
+                     int32_t *ids, float *dist, int64_t *counters, int nthreads) {
+  if (k < 1 || ls < k || ls > 256 || !pol) return 1;
+  q_ctx c = {ix, q, f, aux, k, ls, 0, s0, scan_cap, ids, dist, counters, pol};
+  parallel_for(nq, nthreads, query_range, &c);
+  return 0;
+}
+
+void orc_mlp_infer_batch(const orc_policy *pol, const float *x, int64_t n, float *out) {
+  for (int64_t i = 0; i < n; ++i) orc_mlp_infer(pol, x + i * NFEAT, out + i * (pol->n_ladder + 1));
 }
 
 /* Full final list L (ids, first keys, distances) of the direct search for

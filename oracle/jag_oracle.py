@@ -80,6 +80,8 @@ def lib():
                 "orc_fp8_encode_batch": (None, [P, I64, P]),
                 "orc_fp8_decode_batch": (None, [P, I64, P]),
                 "orc_dist_canon_q_batch": (None, [P, P, P, I32, I64, I64, I64, P]),
+                "orc_query_policy": (I32, [P, P, P, P, I64, I32, I32, I64, I64, P, P, P, P, I32]),
+                "orc_mlp_infer_batch": (None, [P, P, I64, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -356,4 +358,70 @@ def dist_canon_q_rows(q, rows, scale, fmt):
     out = np.empty(q.shape[0], np.float32)
     lib().orc_dist_canon_q_batch(_p(q), _p(rows), _p(scale), int(fmt), q.shape[0], q.shape[1], rows.shape[1],
                                  _p(out))
+    return out
+
+
+POL_PLAIN, POL_LEARNED, POL_FORCED = 0, 1, 2
+NFEAT = 12
+
+
+class _Policy(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("h0", C.c_int32), ("w_bf16", C.c_void_p), ("b_f32", C.c_void_p),
+                ("tau", C.c_float), ("stop_scale", C.c_float), ("n_ladder", C.c_int32),
+                ("ladder", C.c_int32 * 16), ("forced", C.c_void_p), ("features", C.c_void_p),
+                ("decisions", C.c_void_p)]
+
+
+def split_params(theta, nl):
+    """BF16 weight codes (W1, W2, W3 concatenated) and fp32 biases (b1, b2,
+    b3) of a flat fp32 parameter vector (layout of oracle/jag_mlp.py)."""
+    theta = np.asarray(theta, np.float32)
+    h, f = 64, 12
+    sizes = [h * f, h, h * h, h, (nl + 1) * h, nl + 1]
+    parts, off = [], 0
+    for sz in sizes:
+        parts.append(theta[off:off + sz])
+        off += sz
+    w = np.concatenate([parts[0], parts[2], parts[4]])
+    b = np.concatenate([parts[1], parts[3], parts[5]]).astype(np.float32)
+    return bf16_encode(w), b
+
+
+class Policy:
+    """Host-side policy for orc_query_policy."""
+
+    def __init__(self, mode, h0=8, theta=None, ladder=(16, 24, 32, 48, 64, 96, 128, 192, 256), tau=0.0,
+                 stop_scale=64.0, forced=None, nq=0, want_features=False, want_decisions=False):
+        nl = len(ladder)
+        self.nl = nl
+        if theta is None:
+            theta = np.zeros(64 * 12 + 64 + 64 * 64 + 64 + (nl + 1) * 64 + nl + 1, np.float32)
+        self.w, self.b = split_params(theta, nl)
+        self.forced = None if forced is None else np.ascontiguousarray(forced, np.int32)
+        self.features = np.zeros((nq, NFEAT), np.float32) if want_features else None
+        self.decisions = np.zeros((nq, 4), np.int32) if want_decisions else None
+        lad = (C.c_int32 * 16)(*([int(v) for v in ladder] + [0] * (16 - nl)))
+        self.s = _Policy(int(mode), int(h0), _p(self.w), _p(self.b), float(tau), float(stop_scale), nl, lad,
+                         _p(self.forced), _p(self.features), _p(self.decisions))
+
+
+def query_policy(ix: Index, q, filters, aux, k, ls, pol: Policy, s0=0, scan_cap=8192, nthreads=None):
+    q = _c(q, np.float32)
+    nq = q.shape[0]
+    f = np.ascontiguousarray(filters)
+    aux = _c(aux, np.uint8)
+    ids = np.empty((nq, k), np.int32)
+    dist = np.empty((nq, k), np.float32)
+    cnt = np.zeros((nq, 4), np.int64)
+    rc = lib().orc_query_policy(ix.ref(), _p(q), _p(f), _p(aux), nq, k, ls, int(s0), int(scan_cap),
+                                C.byref(pol.s), _p(ids), _p(dist), _p(cnt), nthreads or default_threads())
+    if rc:
+        raise ValueError("invalid policy query arguments")
+    return ids, dist, cnt
+
+
+def mlp_infer(pol: Policy, X):
+    X = _c(np.atleast_2d(X), np.float32)
+    out = np.empty((X.shape[0], pol.nl + 1), np.float32)
+    lib().orc_mlp_infer_batch(C.byref(pol.s), _p(X), X.shape[0], _p(out))
     return out
