@@ -113,6 +113,49 @@ typedef struct jag_index jag_index;   /* opaque */
 /* Flags of jag_search_args.flags. */
 #define JAG_SEARCH_SCAN_ALL 0x1  /* answer every query by the exact scan      */
 
+/* Learned beam width and stop hop (an extension; the paper's search uses
+ * one fixed beam l_s).  A graph-routed query runs h0 hops of Algorithm 1 at
+ * the call's beam; then 12 features of its state go through a small network
+ * (12 -> 64 ReLU -> 64 ReLU -> n_ladder + 1): the largest of the first
+ * n_ladder outputs picks a beam from the ladder, the last output times
+ * stop_scale (rounded to an integer, at least h0) is a hop count after which
+ * the search stops.  If the two largest beam outputs differ by less than tau
+ * the call's beam is kept and there is no stop hop.  The new beam is at most
+ * the call's beam (a larger choice is taken as the call's beam) and L is cut
+ * to it: the search only ever shrinks L, so a point it has set aside can
+ * never qualify again and the visited set may still forget.  Features (exact integer / fp32 arithmetic): bucket
+ * 0.05 * bit-length(est + 1) of the estimated passing count; filter kind one
+ * hot (label, int range, float range, subset, boolean); passing fraction of
+ * L; 0.125 * lg(d) of the best, k-th passing (or last) and last distances,
+ * lg(x) = (bits(x) >> 16) / 128 - 127; answers found / k; expanded prefix
+ * of L / |L|.  Inference: BF16 weights, fp32 fma accumulation over the
+ * inputs in order from the bias. */
+#define JAG_POLICY_PLAIN 0
+#define JAG_POLICY_LEARNED 1
+#define JAG_POLICY_FORCED 2      /* beam / stop per query from `forced`        */
+#define JAG_MLP_FEATURES 12
+#define JAG_MLP_HIDDEN 64
+
+typedef struct jag_policy {
+  int32_t mode;                /* JAG_POLICY_*                                  */
+  int32_t h0;                  /* hops before the decision, >= 1                */
+  const uint16_t *w_bf16;      /* device: W1 [64][12], W2 [64][64],
+                                  W3 [n_ladder+1][64], BF16 codes, row-major    */
+  const float *b_f32;          /* device: b1 [64], b2 [64], b3 [n_ladder+1]     */
+  float tau;                   /* least margin of the winning beam output       */
+  float stop_scale;            /* stop hop = rint(output * stop_scale); <= 0:
+                                  no stop hop                                   */
+  int32_t n_ladder;            /* beam classes, 1..16                           */
+  int32_t ladder[16];          /* beam of each class, each in [k, 256]; a beam
+                                  above the call's beam acts as the call's beam */
+  const int32_t *forced;       /* device [nq][2] (beam, stop; <= 0: none), FORCED;
+                                  a beam is taken into [k, call's beam]         */
+  float *features;             /* device [nq][12] out, or NULL                  */
+  int32_t *decisions;          /* device [nq][4] out, or NULL: final beam, stop
+                                  hop (0 none), last hop that changed the first
+                                  k entries of L, 1 if the network decided     */
+} jag_policy;
+
 typedef struct jag_search_args {
   const float *queries;        /* [nq][d] fp32, row-major, unpadded            */
   const jag_filter *filters;   /* [nq]                                         */
@@ -137,6 +180,7 @@ typedef struct jag_search_args {
   void *ev_graph_begin;        /* optional cudaEvent_t recorded just before
                                   the graph-search kernel                      */
   void *ev_graph_end;          /* ... and just after it                        */
+  const jag_policy *policy;    /* host struct, or NULL for the plain search    */
 } jag_search_args;
 
 /* Build an index on a device (Algorithms 3-4 run on the GPU; Sec. 3.3 and the
@@ -183,6 +227,38 @@ JAG_API jag_status jag_search_host(jag_index *idx, const jag_search_args *args);
  *     or set s0 = 0.
  * Other errors as jag_search. */
 JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_search_args *args);
+
+/* Training of the policy network on the GPU (an extension, like the policy
+ * itself).  params: device fp32 [P] with P = 64*12 + 64 + 64*64 + 64 +
+ * (nl+1)*64 + (nl+1), laid out W1 [64][12], b1, W2 [64][64], b2,
+ * W3 [nl+1][64], b3 (row-major, output by input).  X: device [m][12]
+ * features, y: device [m] beam classes in [0, nl), t: device [m] stop
+ * targets (hop / stop_scale).  Loss of a batch: mean cross-entropy of the
+ * first nl outputs against y plus lam * mean squared error of the last
+ * output against t.  Every sum is taken in a fixed order, so results repeat
+ * bit for bit.  A y outside [0, nl) makes the loss NaN.  Both calls allocate
+ * temporary device memory (stream-ordered) and return JAG_EINVAL for bad
+ * sizes or NULL pointers, JAG_ENOMEM, JAG_ECUDA. */
+
+/* Loss and gradient d loss / d params of one batch of all m rows (device
+ * outputs grad [P] and loss [1]); asynchronous on stream. */
+JAG_API jag_status jag_mlp_loss_grad(int32_t n_ladder, const float *params, const float *X, const int32_t *y,
+                                     const float *t, int64_t m, float lam, float *grad, float *loss, void *stream);
+
+/* Adam (beta 0.9 / 0.999, eps 1e-8, learning rate lr) over `epochs` passes
+ * of the rows in order, in mini-batches of `batch` rows (the last one may be
+ * shorter).  adam_m / adam_v: device [P] moments, zero before the first
+ * step; adam_step: host in/out count of steps taken (bias correction).
+ * loss_trace: host [epochs] mean batch loss of each pass, or NULL.
+ * Synchronous: returns when params are updated. */
+JAG_API jag_status jag_mlp_train(int32_t n_ladder, float *params, float *adam_m, float *adam_v, int64_t *adam_step,
+                                 const float *X, const int32_t *y, const float *t, int64_t m, int32_t epochs,
+                                 int32_t batch, float lr, float lam, float *loss_trace, void *stream);
+
+/* Inference blobs of the policy from params: BF16 weights (round to nearest
+ * even) and fp32 biases, device outputs. */
+JAG_API jag_status jag_mlp_export(int32_t n_ladder, const float *params, uint16_t *w_bf16, float *b_f32,
+                                  void *stream);
 
 /* Index facts. */
 typedef struct jag_info {

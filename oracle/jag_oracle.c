@@ -493,10 +493,11 @@ typedef struct {
   const uint16_t *w_bf16;   /* W1 [64][12], W2 [64][64], W3 [nl+1][64], BF16    */
   const float *b_f32;       /* b1 [64], b2 [64], b3 [nl+1]                       */
   float tau;                /* least margin between the two largest beam logits */
-  float stop_scale;         /* stop hop = rint(output * stop_scale)             */
+  float stop_scale;         /* stop hop = rint(output * stop_scale); <= 0: none */
   int32_t n_ladder;         /* beam classes (nl <= 16)                          */
   int32_t ladder[16];       /* beam of each class                               */
-  const int32_t *forced;    /* [nq][2] (beam, stop) for POL_FORCED              */
+  const int32_t *forced;    /* [nq][2] (beam, stop) for POL_FORCED; beams are
+                               taken into [k, ls]                              */
   float *features;          /* [nq][12] out, or NULL                            */
   int32_t *decisions;       /* [nq][4] out: beam, stop, last top-k change, learned */
 } orc_policy;
@@ -563,16 +564,20 @@ static void policy_decide(const orc_policy *pol, const float *f, int fixed, int 
   if (!(margin >= pol->tau)) { *beam = fixed; *stop = 0; *learned = 0; return; }
   float r = rintf(out[nl] * pol->stop_scale);
   int st;
-  if (!(r == r) || r >= 65535.0f) st = 65535;
+  if (!(pol->stop_scale > 0.0f)) st = 0;          /* no stop hop */
+  else if (!(r == r) || r >= 65535.0f) st = 65535;
   else if (r <= (float)h0) st = h0;
   else st = (int)r;
-  *beam = pol->ladder[c]; *stop = st; *learned = 1;
+  *beam = pol->ladder[c] < fixed ? pol->ladder[c] : fixed;
+  *stop = st; *learned = 1;
 }
 
 /* The direct search (as greedy_direct) run in two phases: h0 hops at the
  * fixed beam ls0, then the beam and stop hop of the policy (L is cut to the
- * new beam if longer; the search also ends once stop hops are done).  Tracks
- * the last hop that inserted an entry among the first k. */
+ * new beam if longer; the search also ends once stop hops are done).  The new
+ * beam never exceeds ls0: the search only ever shrinks L, so a point it has
+ * set aside can never qualify again.  Tracks the last hop that inserted an
+ * entry among the first k. */
 static void greedy_policy(const comparator_t *c, int ls0, int k, const orc_policy *pol, const int32_t *forced_q,
                           int64_t est, int kind, entry_t *L, int *len, uint8_t *seen, int64_t *touched,
                           int64_t *ntouched, counters_t *cnt, float *feat, int32_t *dec) {
@@ -627,7 +632,7 @@ static void greedy_policy(const comparator_t *c, int ls0, int k, const orc_polic
       if (pol->mode == POL_LEARNED) {
         policy_decide(pol, f, ls0, pol->h0, &beam, &stop, &learned);
       } else {
-        beam = forced_q[0] > 0 ? forced_q[0] : ls0;
+        beam = forced_q[0] > 0 ? (forced_q[0] < k ? k : forced_q[0] > ls0 ? ls0 : forced_q[0]) : ls0;
         stop = forced_q[1] > 0 ? (forced_q[1] < pol->h0 ? pol->h0 : forced_q[1]) : 0;
         learned = forced_q[0] > 0;
       }

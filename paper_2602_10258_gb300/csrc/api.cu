@@ -160,6 +160,18 @@ jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
   if (a->k < 1 || a->k > a->beam) return fail(JAG_EINVAL, "k must be in [1, beam]");
   if (a->aux_bytes < 0 || (a->aux_bytes > 0 && !a->filter_aux)) return fail(JAG_EINVAL, "bad filter_aux");
   if (a->nq > (int64_t)1 << 31) return fail(JAG_EINVAL, "nq too large");
+  if (a->policy) {
+    const jag_policy *p = a->policy;
+    if (p->mode < JAG_POLICY_PLAIN || p->mode > JAG_POLICY_FORCED) return fail(JAG_EINVAL, "bad policy mode");
+    if (p->mode != JAG_POLICY_PLAIN && p->h0 < 1) return fail(JAG_EINVAL, "policy h0 must be >= 1");
+    if (p->mode == JAG_POLICY_LEARNED) {
+      if (!p->w_bf16 || !p->b_f32) return fail(JAG_EINVAL, "policy weights are NULL");
+      if (p->n_ladder < 1 || p->n_ladder > 16) return fail(JAG_EINVAL, "n_ladder must be in [1, 16]");
+      for (int i = 0; i < p->n_ladder; ++i)
+        if (p->ladder[i] < a->k || p->ladder[i] > 256) return fail(JAG_EINVAL, "ladder beams must be in [k, 256]");
+    }
+    if (p->mode == JAG_POLICY_FORCED && !p->forced) return fail(JAG_EINVAL, "forced policy needs `forced`");
+  }
   int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
   if (hb < 5 || hb > 16) return fail(JAG_EINVAL, "hash_bits must be in [5, 16]");
   if ((size_t)jag::kSearchWarps * jag::warp_smem_bytes(jag::list_slots(a->beam), hb) > kSmemLimit)
@@ -424,6 +436,7 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   L.ntiles = ntiles; L.tile = tile;
   L.rr = L0.rr;
   L.rr_ids = (int32_t *)(base + L0.rr_ids);
+  if (a->policy) { L.policy = *a->policy; L.has_policy = 1; }
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
   L.ev_end = (cudaEvent_t)a->ev_graph_end;
   L.stream = stream;

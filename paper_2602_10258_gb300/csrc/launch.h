@@ -34,6 +34,8 @@ struct SearchLaunch {
   uint32_t *part_id;
   int32_t ntiles;
   int64_t tile;
+  jag_policy policy;       // learned / forced beam and stop hop (has_policy)
+  int32_t has_policy;
   int32_t rr;              // re-ranked candidates per query (BF16 / FP8 rows)
   int32_t *rr_ids;         // [nq][rr]
   cudaEvent_t ev_begin, ev_end;

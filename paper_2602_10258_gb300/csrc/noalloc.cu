@@ -123,6 +123,7 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   L.ntiles = ntiles; L.tile = tile;
   L.rr = rr;
   L.rr_ids = (int32_t *)(base + o_rr);
+  if (a->policy) { L.policy = *a->policy; L.has_policy = 1; }
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
   L.ev_end = (cudaEvent_t)a->ev_graph_end;
   L.stream = stream;

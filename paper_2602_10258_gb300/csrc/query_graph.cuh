@@ -14,15 +14,19 @@ namespace jag {
 // D_F (Algorithm 2) for the graph-routed ones.  With fp32 rows it writes the
 // answers; with BF16 / FP8 rows it leaves the ids of the leading rr passing
 // entries of the final list for the fp32 re-rank.
-template <int CAP, int P, int CPL, int FMT>
+template <int CAP, int P, int CPL, int FMT, bool POL>
 __global__ void __launch_bounds__(kSearchWarps * 32, CPL == 1 ? 8 : 1)
 query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
              const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int rr, int32_t *rr_ids,
-             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work) {
+             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work, jag_policy pol) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(ls);
-  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, hbits), lcap, hbits);
+  const size_t wbytes = warp_smem_bytes(lcap, hbits) + (POL ? 128 * sizeof(float) : 0);
+  uint8_t *wb = smem + warp * wbytes;
+  const WarpSmem S = carve_warp_smem(wb, lcap, hbits);
+  float *hbuf = reinterpret_cast<float *>(wb + warp_smem_bytes(lcap, hbits));
+  const int64_t sample = ix.n < 4096 ? ix.n : 4096;
   for (;;) {
     unsigned long long qi = 0;
     if (lane == 0) qi = atomicAdd(work, 1ull);
@@ -36,7 +40,18 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
     const QueryKey key{f.kind, f.payload, pl.lut_off >= 0 ? lut_base + pl.lut_off : nullptr};
     NoSink sink;
     SearchStats st;
-    const int cnt = greedy_search<CAP, P, CPL, FMT>(ix, key, q, ls, hbits, S, sink, st);
+    int cnt;
+    if constexpr (POL) {
+      const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
+                          : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
+      const PolicyCtx pc{&pol, est, f.kind, k, hbuf,
+                         pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr,
+                         pol.decisions ? pol.decisions + (int64_t)qi * 4 : nullptr,
+                         pol.forced ? pol.forced + (int64_t)qi * 2 : nullptr};
+      cnt = greedy_search<CAP, P, CPL, FMT, true>(ix, key, q, ls, hbits, S, sink, st, &pc);
+    } else {
+      cnt = greedy_search<CAP, P, CPL, FMT, false>(ix, key, q, ls, hbits, S, sink, st);
+    }
     if (FMT == JAG_VEC_F32) {
       write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
     } else {
@@ -54,10 +69,11 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
   }
 }
 
-template <int CAP, int P, int CPL, int FMT>
+template <int CAP, int P, int CPL, int FMT, bool POL>
 static cudaError_t launch_graph_one(const SearchLaunch &L) {
-  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.ls), L.hbits);
-  auto kern = query_kernel<CAP, P, CPL, FMT>;
+  const int lcap = list_slots(L.ls);
+  const size_t smem = (size_t)kSearchWarps * (warp_smem_bytes(lcap, L.hbits) + (POL ? 128 * sizeof(float) : 0));
+  auto kern = query_kernel<CAP, P, CPL, FMT, POL>;
   const int bps = blocks_per_sm(kern, smem);
   if (bps == 0) return cudaErrorInvalidConfiguration;
   const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
@@ -65,22 +81,24 @@ static cudaError_t launch_graph_one(const SearchLaunch &L) {
   if (L.ev_begin) cudaEventRecord(L.ev_begin, L.stream);
   kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lut,
                                                              L.nq, L.k, L.ls, L.hbits, L.rr, L.rr_ids, L.out_ids,
-                                                             L.out_dist, L.counters, L.work);
+                                                             L.out_dist, L.counters, L.work, L.policy);
   if (L.ev_end) cudaEventRecord(L.ev_end, L.stream);
   return cudaGetLastError();
 }
 
-template <int CAP, int FMT>
+template <int CAP, int FMT, bool POL>
 static cudaError_t launch_graph_cap(const SearchLaunch &L, int P, int CPL) {
 #define JAG_GCASE(PP, CC) \
-  if (P == PP && CPL == CC) return launch_graph_one<CAP, PP, CC, FMT>(L);
+  if (P == PP && CPL == CC) return launch_graph_one<CAP, PP, CC, FMT, POL>(L);
   JAG_GCASE(8, 1)
   JAG_GCASE(16, 1)
   JAG_GCASE(32, 1)
   JAG_GCASE(32, 2)
-  JAG_GCASE(32, 4)
-  if constexpr (FMT == JAG_VEC_F32) {
-    JAG_GCASE(32, 8)
+  if constexpr (!POL) {
+    JAG_GCASE(32, 4)
+    if constexpr (FMT == JAG_VEC_F32) {
+      JAG_GCASE(32, 8)
+    }
   }
 #undef JAG_GCASE
   return cudaErrorInvalidValue;
@@ -91,10 +109,14 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L) {
   int P, CPL;
   const int nch = FMT == JAG_VEC_F32 ? L.ix.nchunks : L.ix.qchunks;
   if (!row_mapping(nch, &P, &CPL)) return cudaErrorInvalidValue;
+  if (L.has_policy) {
+    if (list_capacity(L.ls) <= 128) return launch_graph_cap<128, FMT, true>(L, P, CPL);
+    return launch_graph_cap<256, FMT, true>(L, P, CPL);
+  }
   switch (list_capacity(L.ls)) {
-    case 64: return launch_graph_cap<64, FMT>(L, P, CPL);
-    case 128: return launch_graph_cap<128, FMT>(L, P, CPL);
-    case 256: return launch_graph_cap<256, FMT>(L, P, CPL);
+    case 64: return launch_graph_cap<64, FMT, false>(L, P, CPL);
+    case 128: return launch_graph_cap<128, FMT, false>(L, P, CPL);
+    case 256: return launch_graph_cap<256, FMT, false>(L, P, CPL);
     default: return cudaErrorInvalidValue;
   }
 }

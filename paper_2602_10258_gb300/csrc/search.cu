@@ -73,7 +73,8 @@ __device__ __forceinline__ void pad_outputs(int64_t qi, int k, int32_t *out_ids,
 // (estimate) is below s0 goes to the exact scan.
 __global__ void __launch_bounds__(kPrepWarps * 32)
 prep_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, int64_t aux_bytes, int64_t nq,
-            int64_t s0, int64_t cap, int scan_all, QueryPlan *plans, uint8_t *lut_base, int32_t *list_counts, int k,
+            int64_t s0, int64_t cap, int scan_all, int need_est, QueryPlan *plans, uint8_t *lut_base,
+            int32_t *list_counts, int k,
             int32_t *out_ids, float *out_dist, int32_t *counters, uint32_t *status) {
   const int lane = threadIdx.x & 31;
   const int64_t wstride = (int64_t)gridDim.x * kPrepWarps;
@@ -115,7 +116,7 @@ prep_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, int64_t 
     }
     if (scan_all) {
       pl.route = kRouteSkip + 1;   // brute-force scan
-    } else if (s0 > 0) {
+    } else if (s0 > 0 || need_est) {
       if (f.kind == JAG_F_LABEL || f.kind == JAG_F_RANGE_I32 || f.kind == JAG_F_RANGE_F32) {
         int64_t b = 0, e = 0;
         if (lane == 0) {
@@ -134,7 +135,7 @@ prep_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, int64_t 
         e = __shfl_sync(kFull, e, 0);
         pl.begin = b; pl.end = e;
         pl.est = (int32_t)min64(e - b, 0x7FFFFFFF);
-        if (e - b < s0 && e - b <= cap) pl.route = kRouteSlice;
+        if (s0 > 0 && e - b < s0 && e - b <= cap) pl.route = kRouteSlice;
       } else if (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) {
         const int64_t S = ix.n < 4096 ? ix.n : 4096;
         int hits = 0;
@@ -142,7 +143,7 @@ prep_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, int64_t 
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) hits += __shfl_xor_sync(kFull, hits, o);
         pl.est = hits;
-        if ((int64_t)hits * ix.n < s0 * S) {
+        if (s0 > 0 && (int64_t)hits * ix.n < s0 * S) {
           pl.route = kRouteList;
           if (lane == 0) list_counts[qi] = 0;
         }
@@ -712,7 +713,8 @@ cudaError_t run_search(const SearchLaunch &L) {
   {
     int64_t blocks = std::min<int64_t>((L.nq + kPrepWarps - 1) / kPrepWarps, (int64_t)num_sms() * 16);
     prep_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, L.stream>>>(
-        L.ix, L.filters, L.aux, L.aux_bytes, L.nq, L.s0, L.cap, L.scan_all, L.plans, L.lut, L.list_counts, L.k,
+        L.ix, L.filters, L.aux, L.aux_bytes, L.nq, L.s0, L.cap, L.scan_all, L.has_policy, L.plans, L.lut,
+        L.list_counts, L.k,
         L.out_ids, L.out_dist, L.counters, L.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

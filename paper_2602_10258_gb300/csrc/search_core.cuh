@@ -281,11 +281,141 @@ struct SearchStats {
   int hops, seen, dcs;
 };
 
+// ---------------------------------------------------------------------------
+// learned beam width and stop hop
+// ---------------------------------------------------------------------------
+
+// Monotone stand-in for log2 from the float encoding: (bits >> 16)/128 - 127.
+__device__ __forceinline__ float flog_bits(float x) {
+  return __fsub_rn(__fmul_rn((float)(f2u(x) >> 16), 0.0078125f), 127.f);
+}
+
+__device__ __forceinline__ float bf16_value(uint16_t h) { return u2f((uint32_t)h << 16); }
+
+// Outcome of the policy at the decision hop.
+struct PolicyOut {
+  int beam, stop, learned;
+};
+
+// Features of the list L[0..cnt) after the decision hop and the policy's
+// beam / stop (every lane returns the same).  hbuf: 128 floats of the warp.
+__device__ __noinline__ static PolicyOut policy_decide(const jag_policy &pol, const WarpSmem &S, float *hbuf, int cnt, int k,
+                                   int64_t est, int32_t kind, int fixed, float *feat_out, const int32_t *forced_q) {
+  const int lane = threadIdx.x & 31;
+  // passing prefix and first unexpanded entry
+  int np = cnt;
+  for (int b = 0; b < cnt; b += 32) {
+    const int j = b + lane;
+    const uint32_t m = __ballot_sync(kFull, j < cnt && (S.bkey[j] >> 32) != 0);
+    if (m) { np = b + __ffs(m) - 1; break; }
+  }
+  int fu = first_unexpanded(S.bid, cnt, 0);
+  if (fu < 0) fu = cnt;
+  const uint32_t e = est > 0x7FFFFFFE ? 0x7FFFFFFFu : (uint32_t)est + 1u;
+  const int kk = np < k ? np : k;
+  float f[JAG_MLP_FEATURES];
+  f[0] = __fmul_rn((float)(32 - __clz(e)), 0.05f);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) f[1 + i] = (kind == i + 1) ? 1.f : 0.f;
+  f[6] = __fdiv_rn((float)np, (float)cnt);
+  f[7] = __fmul_rn(flog_bits(u2f((uint32_t)S.bkey[0])), 0.125f);
+  f[8] = __fmul_rn(flog_bits(u2f((uint32_t)S.bkey[np > 0 ? kk - 1 : cnt - 1])), 0.125f);
+  f[9] = __fdiv_rn((float)kk, (float)k);
+  f[10] = __fdiv_rn((float)fu, (float)cnt);
+  f[11] = __fmul_rn(flog_bits(u2f((uint32_t)S.bkey[cnt - 1])), 0.125f);
+  if (feat_out) {
+#pragma unroll
+    for (int i = 0; i < JAG_MLP_FEATURES; ++i)
+      if (lane == i) feat_out[i] = f[i];
+  }
+  PolicyOut o;
+  if (pol.mode == JAG_POLICY_FORCED) {
+    const int fb = forced_q[0], fs = forced_q[1];
+    o.beam = fb > 0 ? (fb < k ? k : fb > fixed ? fixed : fb) : fixed;
+    o.stop = fs > 0 ? (fs < pol.h0 ? pol.h0 : fs) : 0;
+    o.learned = fb > 0 ? 1 : 0;
+    return o;
+  }
+  // network: lanes hold neurons lane and lane + 32 of each hidden layer
+  const uint16_t *w1 = pol.w_bf16, *w2 = w1 + JAG_MLP_HIDDEN * JAG_MLP_FEATURES, *w3 = w2 + JAG_MLP_HIDDEN * JAG_MLP_HIDDEN;
+  const float *b1 = pol.b_f32, *b2 = b1 + JAG_MLP_HIDDEN, *b3 = b2 + JAG_MLP_HIDDEN;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int n = lane + 32 * h;
+    float acc = b1[n];
+#pragma unroll
+    for (int i = 0; i < JAG_MLP_FEATURES; ++i) acc = __fmaf_rn(bf16_value(w1[n * JAG_MLP_FEATURES + i]), f[i], acc);
+    hbuf[n] = acc > 0.f ? acc : 0.f;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int n = lane + 32 * h;
+    float acc = b2[n];
+    for (int i = 0; i < JAG_MLP_HIDDEN; ++i) acc = __fmaf_rn(bf16_value(w2[n * JAG_MLP_HIDDEN + i]), hbuf[i], acc);
+    hbuf[JAG_MLP_HIDDEN + n] = acc > 0.f ? acc : 0.f;
+  }
+  __syncwarp();
+  const int nl = pol.n_ladder;
+  float out = -INFINITY;
+  if (lane <= nl) {
+    float acc = b3[lane];
+    for (int i = 0; i < JAG_MLP_HIDDEN; ++i)
+      acc = __fmaf_rn(bf16_value(w3[lane * JAG_MLP_HIDDEN + i]), hbuf[JAG_MLP_HIDDEN + i], acc);
+    out = acc;
+  }
+  __syncwarp();
+  // largest beam output (lowest class on a tie), then the runner-up
+  float v = lane < nl ? out : -INFINITY;
+  int c = lane;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const float ov = __shfl_xor_sync(kFull, v, off);
+    const int oc = __shfl_xor_sync(kFull, c, off);
+    if (ov > v || (ov == v && oc < c)) { v = ov; c = oc; }
+  }
+  float v2 = (lane < nl && lane != c) ? out : -INFINITY;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v2 = fmaxf(v2, __shfl_xor_sync(kFull, v2, off));
+  const float margin = __fsub_rn(v, v2);
+  const float sv = __shfl_sync(kFull, out, nl);
+  if (!(margin >= pol.tau)) {
+    o.beam = fixed; o.stop = 0; o.learned = 0;
+    return o;
+  }
+  const float r = rintf(__fmul_rn(sv, pol.stop_scale));
+  int st;
+  if (!(pol.stop_scale > 0.f)) st = 0;
+  else if (!(r == r) || r >= 65535.f) st = 65535;
+  else if (r <= (float)pol.h0) st = pol.h0;
+  else st = (int)r;
+  o.beam = pol.ladder[c] < fixed ? pol.ladder[c] : fixed;
+  o.stop = st; o.learned = 1;
+  return o;
+}
+
+// Per-search policy context passed to greedy_search.
+struct PolicyCtx {
+  const jag_policy *pol;   // nullptr: plain search
+  int64_t est;
+  int32_t kind;
+  int32_t k;
+  float *hbuf;             // 128 floats of the warp
+  float *feat_out;         // [12] or nullptr
+  int32_t *dec_out;        // [4] or nullptr
+  const int32_t *forced_q; // [2] or nullptr
+};
+
 // Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
 // hold the final list L (count returned).
-template <int CAP, int P, int CPL, int FMT, class KeyFn, class Sink>
+template <int CAP, int P, int CPL, int FMT, bool POL = false, class KeyFn, class Sink>
 __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunks<CPL, FMT> &q, int ls,
-                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st) {
+                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st,
+                             const PolicyCtx *pc = nullptr) {
+  const int ls0 = ls;
+  int stop = 0, learned = 0;
+  int last_change = 0;
+  bool decided = false;
   const int lane = threadIdx.x & 31;
   const uint32_t hsize = 1u << hbits;
   for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
@@ -303,7 +433,9 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
   __syncwarp();
   int cnt = 1, start = 0;
   st.hops = 0; st.seen = 0; st.dcs = 1;
+  if (POL && pc->feat_out && lane < JAG_MLP_FEATURES) pc->feat_out[lane] = 0.f;
   for (;;) {
+    if (POL && stop > 0 && st.hops >= stop) break;
     const int sel = first_unexpanded(S.bid, cnt, start);
     if (sel < 0) break;
     const uint32_t pid = S.bid[sel];
@@ -355,14 +487,27 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       int r0;
       cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0);
       rmin = r0 < rmin ? r0 : rmin;
+      if (POL && r0 < pc->k) last_change = st.hops;
     }
     start = (sel + 1) < rmin ? (sel + 1) : rmin;
+    if (POL && !decided && pc->pol->mode != JAG_POLICY_PLAIN && st.hops == pc->pol->h0) {
+      const PolicyOut o = policy_decide(*pc->pol, S, pc->hbuf, cnt, pc->k, pc->est, pc->kind, ls0, pc->feat_out,
+                                        pc->forced_q);
+      ls = o.beam;
+      stop = o.stop;
+      learned = o.learned;
+      if (cnt > ls) cnt = ls;
+      decided = true;
+    }
     if (fill > (hsize >> 1) + (hsize >> 2)) {
       __syncwarp();
       for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
       fill = 0;
       __syncwarp();
     }
+  }
+  if (POL && pc->dec_out && lane == 0) {
+    pc->dec_out[0] = ls; pc->dec_out[1] = stop; pc->dec_out[2] = last_change; pc->dec_out[3] = learned;
   }
   return cnt;
 }

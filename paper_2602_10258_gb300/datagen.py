@@ -249,12 +249,15 @@ def make_range_i32(n=10_000, d=32, nq=200, seed=0, width=100, domain=1000) -> Wo
 
 
 def make_label_zipf(n=1_000_000, d=128, nq=10_000, seed=0, n_labels=1000, s=1.1,
-                    n_centres=100) -> Workload:
+                    n_centres=100, query_seed=None) -> Workload:
+    """query_seed: draw the queries from another seed over the same base set
+    (held-out or training queries); None = seed."""
     centres = mixture_centres(_rng(seed, 10), n_centres, d)
     x = gaussian_mixture(_rng(seed, 11), n, d, centres)
     labels = zipf_labels(_rng(seed, 12), n, n_labels, s)
-    q = gaussian_mixture(_rng(seed, 13), nq, d, centres)
-    ql = zipf_labels(_rng(seed, 14), nq, n_labels, s)
+    qs = seed if query_seed is None else query_seed
+    q = gaussian_mixture(_rng(qs, 13), nq, d, centres)
+    ql = zipf_labels(_rng(qs, 14), nq, n_labels, s)
     return Workload("label_zipf", x, q, filters_label(ql), BoolFilterBuilder().aux(),
                     attr_i32=labels, dist_a=F_LABEL,
                     params=dict(n=n, d=d, nq=nq, seed=seed, n_labels=n_labels, s=s,
@@ -371,3 +374,14 @@ def random_bool_filters(rng, nq, nbits, m, p_true=0.5):
         table = (rng.random(1 << m) < p_true).astype(np.uint8)
         entries.append(bb.add(vm, table))
     return filters_bool(entries), bb.aux()
+
+
+def mlp_init_params(nl, seed=0):
+    """Seeded initial parameters of the policy network (12 -> 64 -> 64 ->
+    nl + 1), flat fp32 in the layout W1, b1, W2, b2, W3, b3: He-scaled normal
+    weights, zero biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = [rng.standard_normal((64, 12)) * np.sqrt(2.0 / 12), np.zeros(64),
+             rng.standard_normal((64, 64)) * np.sqrt(2.0 / 64), np.zeros(64),
+             rng.standard_normal((nl + 1, 64)) * np.sqrt(1.0 / 64), np.zeros(nl + 1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)

@@ -21,6 +21,8 @@ JAG_OK, JAG_EINVAL, JAG_ENOMEM, JAG_ECUDA, JAG_ETIMEOUT, JAG_EUNSUPPORTED = rang
 JAG_F_NONE, JAG_F_LABEL, JAG_F_RANGE_I32, JAG_F_RANGE_F32, JAG_F_SUBSET, JAG_F_BOOL = range(6)
 JAG_VEC_F32, JAG_VEC_BF16, JAG_VEC_FP8 = range(3)
 JAG_SEARCH_SCAN_ALL = 0x1
+JAG_POLICY_PLAIN, JAG_POLICY_LEARNED, JAG_POLICY_FORCED = range(3)
+MLP_FEATURES, MLP_HIDDEN = 12, 64
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
 
@@ -46,7 +48,15 @@ class SearchArgs(C.Structure):
                 ("out_ids", C.c_void_p), ("out_dist", C.c_void_p), ("stream", C.c_void_p),
                 ("s0", C.c_int64), ("scan_cap", C.c_int64), ("counters", C.c_void_p),
                 ("flags", C.c_int32), ("hash_bits", C.c_int32), ("ev_graph_begin", C.c_void_p),
-                ("ev_graph_end", C.c_void_p)]
+                ("ev_graph_end", C.c_void_p), ("policy", C.c_void_p)]
+
+
+class PolicyStruct(C.Structure):
+    """Mirror of jag_policy."""
+    _fields_ = [("mode", C.c_int32), ("h0", C.c_int32), ("w_bf16", C.c_void_p), ("b_f32", C.c_void_p),
+                ("tau", C.c_float), ("stop_scale", C.c_float), ("n_ladder", C.c_int32),
+                ("ladder", C.c_int32 * 16), ("forced", C.c_void_p), ("features", C.c_void_p),
+                ("decisions", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -57,7 +67,7 @@ class Info(C.Structure):
 
 EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_search_noalloc", "jag_get_info",
             "jag_get_graph", "jag_get_thresholds", "jag_get_stored_rows", "jag_free", "jag_last_error",
-            "jag_version"]
+            "jag_version", "jag_mlp_loss_grad", "jag_mlp_train", "jag_mlp_export"]
 
 _lib = None
 _lock = threading.Lock()
@@ -101,6 +111,13 @@ def load(build_if_missing: bool = True):
             L.jag_last_error.restype = C.c_char_p
             L.jag_version.argtypes = []
             L.jag_version.restype = C.c_char_p
+            I32, I64, F = C.c_int32, C.c_int64, C.c_float
+            L.jag_mlp_loss_grad.argtypes = [I32, P, P, P, P, I64, F, P, P, P]
+            L.jag_mlp_loss_grad.restype = C.c_int
+            L.jag_mlp_train.argtypes = [I32, P, P, P, C.POINTER(C.c_int64), P, P, P, I64, I32, I32, F, F, P, P]
+            L.jag_mlp_train.restype = C.c_int
+            L.jag_mlp_export.argtypes = [I32, P, P, P, P]
+            L.jag_mlp_export.restype = C.c_int
             _lib = L
     return _lib
 
@@ -193,7 +210,7 @@ def _args(nq, k, beam, s0, scan_cap, flags, hash_bits, aux_bytes):
 
 
 def jag_search(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=None, stream=None,
-               s0=-1, scan_cap=0, flags=0, hash_bits=0, ev_begin=None, ev_end=None):
+               s0=-1, scan_cap=0, flags=0, hash_bits=0, ev_begin=None, ev_end=None, policy=None):
     """Device-pointer search: every tensor argument is a CUDA tensor (queries
     float32 [nq, d], filters uint8 [nq*16], aux uint8, out_ids int32 [nq, k],
     out_dist float32 [nq, k], counters int32 [nq, 4] or None).  Asynchronous
@@ -211,11 +228,13 @@ def jag_search(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=No
     a.stream = st.cuda_stream
     a.ev_graph_begin = None if ev_begin is None else ev_begin.cuda_event
     a.ev_graph_end = None if ev_end is None else ev_end.cuda_event
+    ps = None if policy is None else policy.struct()
+    a.policy = None if ps is None else C.addressof(ps)
     _check(L.jag_search(h, C.byref(a)))
 
 
 def jag_search_noalloc(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=None, stream=None,
-                       s0=-1, scan_cap=0, flags=0, hash_bits=0):
+                       s0=-1, scan_cap=0, flags=0, hash_bits=0, policy=None):
     """jag_search without any device allocation: the library's fixed scratch
     area is used instead (for callers that cannot allocate while searching).
     Calls share that area, so calls whose device work overlaps race; a call
@@ -231,6 +250,8 @@ def jag_search_noalloc(h, queries, filters, aux, k, beam, out_ids, out_dist, cou
     a.counters = None if counters is None else counters.data_ptr()
     st = stream if stream is not None else torch.cuda.current_stream(queries.device)
     a.stream = st.cuda_stream
+    ps = None if policy is None else policy.struct()
+    a.policy = None if ps is None else C.addressof(ps)
     _check(L.jag_search_noalloc(h, C.byref(a)))
 
 
@@ -295,7 +316,7 @@ class Index:
         return jag_get_stored_rows(self.h)
 
     def search(self, queries, filters, aux, k, beam, counters=False, stream=None, s0=-1, scan_cap=0,
-               flags=0, hash_bits=0, ev_begin=None, ev_end=None):
+               flags=0, hash_bits=0, ev_begin=None, ev_end=None, policy=None):
         """Search with device tensors; filters/aux may be numpy (copied to the
         device).  Returns CUDA tensors (ids, dist, counters or None)."""
         import torch
@@ -307,7 +328,7 @@ class Index:
         dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
         cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev) if counters else None
         jag_search(self.h, queries, ft, at, k, beam, ids, dist, cnt, stream, s0, scan_cap, flags,
-                   hash_bits, ev_begin, ev_end)
+                   hash_bits, ev_begin, ev_end, policy)
         return ids, dist, cnt
 
     def search_host(self, queries, filters, aux, k, beam, **kw):
@@ -340,3 +361,96 @@ def aux_to_device(aux, device):
     if isinstance(aux, torch.Tensor):
         return aux.to(device)
     return torch.from_numpy(np.ascontiguousarray(aux, np.uint8).copy()).to(device)
+
+
+# ---------------------------------------------------------------------------
+# learned beam width / stop hop
+# ---------------------------------------------------------------------------
+
+LADDER = (16, 24, 32, 48, 64, 96, 128, 192, 256)
+
+
+def mlp_n_params(nl):
+    h, f = MLP_HIDDEN, MLP_FEATURES
+    return h * f + h + h * h + h + (nl + 1) * h + nl + 1
+
+
+class Policy:
+    """Search policy passed to jag_search (``policy=``): device tensors for the
+    BF16 weights / fp32 biases (LEARNED), the per-query (beam, stop) pairs
+    (FORCED) and the optional feature / decision outputs."""
+
+    def __init__(self, mode, h0=8, w_bf16=None, b_f32=None, tau=0.0, stop_scale=64.0, ladder=LADDER,
+                 forced=None, features=None, decisions=None):
+        self.mode, self.h0, self.tau, self.stop_scale = int(mode), int(h0), float(tau), float(stop_scale)
+        self.ladder = tuple(int(v) for v in ladder)
+        self.w_bf16, self.b_f32, self.forced = w_bf16, b_f32, forced
+        self.features, self.decisions = features, decisions
+
+    @staticmethod
+    def _ptr(t):
+        return None if t is None else t.data_ptr()
+
+    def struct(self):
+        p = PolicyStruct()
+        p.mode, p.h0, p.tau, p.stop_scale = self.mode, self.h0, self.tau, self.stop_scale
+        p.n_ladder = len(self.ladder)
+        for i, v in enumerate(self.ladder):
+            p.ladder[i] = v
+        p.w_bf16, p.b_f32 = self._ptr(self.w_bf16), self._ptr(self.b_f32)
+        p.forced, p.features, p.decisions = self._ptr(self.forced), self._ptr(self.features), self._ptr(self.decisions)
+        self._s = p
+        return p
+
+    @classmethod
+    def learned(cls, params, ladder=LADDER, h0=8, tau=0.0, stop_scale=64.0, stream=None, **kw):
+        """Policy from a flat fp32 parameter tensor (CUDA): the weights are
+        exported to BF16 by jag_mlp_export."""
+        import torch
+        nl = len(ladder)
+        nw = MLP_HIDDEN * MLP_FEATURES + MLP_HIDDEN * MLP_HIDDEN + (nl + 1) * MLP_HIDDEN
+        w = torch.empty(nw, dtype=torch.int16, device=params.device)
+        b = torch.empty(2 * MLP_HIDDEN + nl + 1, dtype=torch.float32, device=params.device)
+        mlp_export(nl, params, w, b, stream)
+        return cls(JAG_POLICY_LEARNED, h0=h0, w_bf16=w, b_f32=b, tau=tau, stop_scale=stop_scale, ladder=ladder, **kw)
+
+
+def _stream_ptr(stream, device):
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    return st.cuda_stream
+
+
+def mlp_loss_grad(nl, params, X, y, t, lam, stream=None):
+    """(loss, grad) of the network over all rows (CUDA tensors)."""
+    import torch
+    g = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(load().jag_mlp_loss_grad(int(nl), params.data_ptr(), X.data_ptr(), y.data_ptr(), t.data_ptr(),
+                                    int(X.shape[0]), float(lam), g.data_ptr(), loss.data_ptr(),
+                                    _stream_ptr(stream, params.device)))
+    return loss, g
+
+
+class Trainer:
+    """Adam state of one parameter tensor; ``run`` trains in place."""
+
+    def __init__(self, nl, params):
+        import torch
+        self.nl, self.params = int(nl), params
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.step = C.c_int64(0)
+
+    def run(self, X, y, t, epochs, batch, lr, lam, stream=None):
+        trace = np.zeros(max(int(epochs), 1), np.float32)
+        _check(load().jag_mlp_train(self.nl, self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                    C.byref(self.step), X.data_ptr(), y.data_ptr(), t.data_ptr(), int(X.shape[0]),
+                                    int(epochs), int(batch), float(lr), float(lam), trace.ctypes.data,
+                                    _stream_ptr(stream, self.params.device)))
+        return trace[:int(epochs)]
+
+
+def mlp_export(nl, params, w_bf16, b_f32, stream=None):
+    _check(load().jag_mlp_export(int(nl), params.data_ptr(), w_bf16.data_ptr(), b_f32.data_ptr(),
+                                 _stream_ptr(stream, params.device)))

@@ -60,7 +60,8 @@ def _c_layout(struct, fields):
 
 @pytest.mark.parametrize("struct,cls", [("jag_build_params", jag.BuildParams),
                                         ("jag_search_args", jag.SearchArgs),
-                                        ("jag_info", jag.Info)])
+                                        ("jag_info", jag.Info),
+                                        ("jag_policy", jag.PolicyStruct)])
 def test_record_layouts_match_header(struct, cls):
     fields = [f for f, _ in cls._fields_]
     lay = _c_layout(struct, fields)
@@ -92,3 +93,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.jag_build(C.byref(p), C.byref(h)) == jag.JAG_EINVAL
     assert b"d must be" in lib.jag_last_error()
     lib.jag_free(None)
+    assert lib.jag_mlp_loss_grad(0, None, None, None, None, 1, 0.0, None, None, None) == jag.JAG_EINVAL
+    assert lib.jag_mlp_export(17, None, None, None, None) == jag.JAG_EINVAL
+    step = C.c_int64(0)
+    assert lib.jag_mlp_train(9, None, None, None, C.byref(step), None, None, None, 1, 1, 1, 1e-3, 0.0, None,
+                             None) == jag.JAG_EINVAL

@@ -105,13 +105,48 @@ def test_forced_beam_switch_invariants(small):
     w, ix = small
     nq = len(w.q)
     rng = np.random.default_rng(9)
-    beams = rng.choice([10, 16, 24, 32, 48, 64], nq)
+    beams = rng.choice([10, 16, 24, 32, 48, 64, 80, 200], nq)
     forced = np.stack([beams, np.zeros(nq)], axis=1).astype(np.int32)
     pol = O.Policy(O.POL_FORCED, h0=6, forced=forced, nq=nq, want_decisions=True)
-    ids, dist, cnt = O.query_policy(ix, w.q, w.filters, w.aux, 10, 32, pol)
-    assert (pol.decisions[:, 0] == beams).all()
+    ids, dist, cnt = O.query_policy(ix, w.q, w.filters, w.aux, 10, 64, pol)
+    assert (pol.decisions[:, 0] == np.minimum(beams, 64)).all()        # the beam only shrinks
     lab = (w.filters["payload"] & np.uint64(0xFFFFFFFF)).astype(np.int64)
     for i in range(nq):
         m = ids[i] >= 0
         assert (w.attr_i32[ids[i][m]] == lab[i]).all()
         assert (np.diff(dist[i][m]) >= 0).all()
+
+
+@pytest.mark.parametrize("c,stop_out,scale", [(0, 0.9, 64.0), (4, -3.0, 64.0), (8, 0.2, 64.0), (3, 5.0, 0.0),
+                                              (6, 2000.0, 64.0)])
+def test_constant_network_is_a_forced_policy(small, c, stop_out, scale):
+    """With W3 = 0 the outputs are b3 exactly (each fma adds an exact zero):
+    the policy then equals a FORCED one with beam min(ladder[c], l_s) and stop
+    rint(b3[nl] * scale), at least h0, at most 65535, none if scale <= 0."""
+    w, ix = small
+    nq = len(w.q)
+    ladder = (16, 24, 32, 48, 64, 96, 128, 192, 256)
+    theta = M.init_params(NL, seed=11).astype(np.float32)
+    nw3 = (NL + 1) * 64
+    off3 = 64 * 12 + 64 + 64 * 64 + 64
+    theta[off3:off3 + nw3] = 0.0
+    b3 = np.zeros(NL + 1, np.float32)
+    b3[c] = 1.0
+    b3[NL] = stop_out
+    theta[off3 + nw3:] = b3
+    h0 = 6
+    pol = O.Policy(O.POL_LEARNED, h0=h0, theta=theta, ladder=ladder, tau=0.5, stop_scale=scale, nq=nq,
+                   want_decisions=True)
+    a = O.query_policy(ix, w.q, w.filters, w.aux, 10, 128, pol)
+    stop = 0 if scale <= 0 else int(min(max(np.rint(np.float32(stop_out) * np.float32(scale)), h0), 65535))
+    forced = np.tile(np.array([[ladder[c], stop]], np.int32), (nq, 1))
+    fp = O.Policy(O.POL_FORCED, h0=h0, forced=forced, nq=nq, want_decisions=True)
+    b = O.query_policy(ix, w.q, w.filters, w.aux, 10, 128, fp)
+    assert all((x == y).all() for x, y in zip(a, b))
+    assert (pol.decisions == fp.decisions).all()
+    assert (pol.decisions[:, 1] == stop).all() and (pol.decisions[:, 0] == min(ladder[c], 128)).all()
+    # margin 1.0 below tau: the fixed beam, no stop
+    pol2 = O.Policy(O.POL_LEARNED, h0=h0, theta=theta, ladder=ladder, tau=1.5, stop_scale=scale, nq=nq,
+                    want_decisions=True)
+    O.query_policy(ix, w.q, w.filters, w.aux, 10, 128, pol2)
+    assert (pol2.decisions[:, 0] == 128).all() and (pol2.decisions[:, 1] == 0).all() and (pol2.decisions[:, 3] == 0).all()
