@@ -335,6 +335,14 @@ def run_ours(args):
         log("%s: beam %s, %.0f QPS" % (fname, forms[fname]["beam"], forms[fname]["qps"]))
     forms["fp32"] = {"beam": chosen, "qps": round(value / world, 1), "recall": sweep[chosen],
                      "graph_kernel_ms": round(float(kern_ms.mean()), 3)}
+    if not args.no_learned:
+        forms["bf16_learned"] = measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_ids, gt_d,
+                                                flush, stream, steps=min(args.steps, 50))
+        log("bf16+learned: %s" % {k: v for k, v in forms["bf16_learned"].items() if k in ("beam", "stop_scale", "qps")})
+    serving = None
+    if not args.no_serve:
+        serving = measure_serving(jag, idx, w, chosen, band, gt_ids, gt_d, value / world)
+        log("serving: %s" % {k: (v["p50_ms"], v["p99_ms"], v["achieved_qps"]) for k, v in serving.items()})
 
     cpu, ocnt = None, None
     if rank == 0 and not args.no_cpu:
@@ -382,6 +390,7 @@ def run_ours(args):
                 "recall": float(np.nanmean(e2e_rec))},
         "cpu_baseline": cpu,
         "forms": forms,
+        "serving": serving,
         "clocks": clk.summary(),
         "gpu_launches": int(args.steps * 3),
     }
@@ -432,6 +441,116 @@ def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stre
     kms = float(np.mean([ka.elapsed_time(kb) for _, _, ka, kb in ts]))
     return {"beam": chosen, "qps": round(nq / (ms / 1000.0), 1), "ms_per_step": round(ms, 4),
             "graph_kernel_ms": round(kms, 3), "recall": per, "steps": steps}
+
+
+def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_ids, gt_d, flush, stream,
+                    n_train=20000, steps=50):
+    """BF16 rows + the learned stop hop.  Traces: n_train training queries
+    (another query seed, same base set) searched at each base beam; the
+    network learns the hop of each query's last change among its first k
+    answers (plus 8 hops), in units of 1/64 hop.  Then the fastest (base beam,
+    stop scale) whose recall@10 is >= 0.95 in every band, timed like the
+    other forms; the fixed-beam BF16 form is its baseline."""
+    import torch
+    from paper_2602_10258_gb300 import datagen as D
+    from paper_2602_10258_gb300 import policy as PL
+    dev = q.device
+    fidx = jag.Index.from_workload(w, R=R, graph=graph_host, entry=entry, storage=jag.JAG_VEC_BF16, device=local)
+    wt = D.make_label_zipf(n=w.n, d=w.d, nq=n_train, seed=0, query_seed=101)
+    qt = torch.from_numpy(wt.q).to(dev)
+    ftt = jag.filters_to_device(wt.filters, dev)
+    att = jag.aux_to_device(wt.aux, dev)
+    nl = len(jag.LADDER)
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev)
+    t0 = time.time()
+    cands = []
+    for base in (192, 224, 256):
+        forced = torch.tensor([[base, 0]], dtype=torch.int32, device=dev).repeat(n_train, 1)
+        feats = torch.zeros((n_train, 12), dtype=torch.float32, device=dev)
+        dec = torch.zeros((n_train, 4), dtype=torch.int32, device=dev)
+        pol = jag.Policy(jag.JAG_POLICY_FORCED, h0=32, forced=forced, features=feats, decisions=dec)
+        fidx.search(qt, ftt, att, K, base, s0=0, policy=pol)
+        torch.cuda.synchronize()
+        X = feats
+        y = torch.full((n_train,), nl - 1, dtype=torch.int32, device=dev)    # keep the base beam
+        t = ((dec[:, 2].float() + 8.0) / 64.0).contiguous()
+        params = torch.from_numpy(D.mlp_init_params(nl, 0)).to(dev)
+        tr = jag.Trainer(nl, params)
+        trace = tr.run(X, y, t, epochs=60, batch=512, lr=2e-3, lam=1.0)
+        for scale in (64.0, 80.0, 96.0, 112.0, 128.0):
+            lp = jag.Policy.learned(params, h0=32, tau=0.0, stop_scale=scale)
+            jag.jag_search(fidx.h, q, ft, at, K, base, ids, dd, cnt, stream, s0=S0, policy=lp)
+            torch.cuda.synchronize()
+            rec = recall_at_k(ids.cpu().numpy(), gt_ids, gt_d)
+            per = {name: float(np.mean(rec[(band == j) & ~np.isnan(rec)])) for j, (_, _, name) in enumerate(BANDS)
+                   if ((band == j) & ~np.isnan(rec)).any()}
+            c = cnt.cpu().numpy()
+            g = c[:, 3] == 0
+            cands.append((base, scale, lp, per, float(c[g, 0].mean()), float(trace[-1])))
+    ok = [cd for cd in cands if all(v >= 0.95 for v in cd[3].values())]
+    train_s = time.time() - t0
+
+    def timed(beam, pol):
+        for _ in range(3):
+            jag.jag_search(fidx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, policy=pol)
+        evs = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            jag.jag_search(fidx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, policy=pol)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    best = None
+    for base, scale, lp, per, hops, loss in ok:
+        ms = timed(base, lp)
+        if best is None or ms < best[0]:
+            best = (ms, base, scale, per, hops, loss)
+    fidx.close()
+    if best is None:
+        return {"qps": None, "note": "no (base, scale) reached recall 0.95 in every band",
+                "train_seconds": round(train_s, 1)}
+    ms, base, scale, per, hops, loss = best
+    return {"beam": base, "stop_scale": scale, "h0": 32, "qps": round(nq / (ms / 1000.0), 1),
+            "ms_per_step": round(ms, 4), "recall": per, "mean_hops_graph_route": round(hops, 1),
+            "train": {"queries": n_train, "epochs": 60, "final_loss": round(loss, 4), "seconds": round(train_s, 1)},
+            "steps": steps}
+
+
+def measure_serving(jag, idx, w, beam, band, gt_ids, gt_d, sat_qps, n_req=2000, loads=(0.5, 0.8)):
+    """The serve loop under open-loop Poisson arrivals: request sizes uniform
+    in 1..256 queries (rows of the 10,000-query batch), arrival rate a
+    fraction of the batch search's throughput; p50 / p99 latency from
+    arrival to completion, achieved QPS, and recall per band."""
+    out = {}
+    rng = np.random.default_rng(0)
+    for load in loads:
+        sizes = rng.integers(1, 257, n_req).astype(np.int32)
+        first = np.array([rng.integers(0, len(w.q) - s + 1) for s in sizes], np.int64)
+        rate = load * sat_qps / float(sizes.mean())            # requests per second
+        arrival = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        srv = jag.Server(idx, K, beam, s0=S0, max_queries=1 << 17)
+        t1 = time.perf_counter()
+        ids, dist, lat, devs = srv.replay(arrival, sizes, first, w.q, w.filters, w.aux, timeout_s=300.0)
+        wall = time.perf_counter() - t1
+        info = srv.info()
+        srv.stop()
+        rows = np.unique(np.concatenate([np.arange(f, f + s) for f, s in zip(first, sizes)]))
+        rec = recall_at_k(ids[rows], gt_ids[rows], gt_d[rows])
+        per = {name: float(np.mean(rec[(band[rows] == j) & ~np.isnan(rec)])) for j, (_, _, name) in enumerate(BANDS)
+               if ((band[rows] == j) & ~np.isnan(rec)).any()}
+        out["load_%.1f" % load] = {
+            "offered_qps": round(load * sat_qps, 1), "achieved_qps": round(float(sizes.sum()) / wall, 1),
+            "p50_ms": round(1000 * float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(1000 * float(np.percentile(lat, 99)), 3),
+            "device_p50_ms": round(1000 * float(np.percentile(devs, 50)), 3),
+            "requests": n_req, "queries": int(sizes.sum()), "recall": per, "loop_launches": info["launches"]}
+    return out
 
 
 def stored_distance_error(idx, w, gt_ids, fcode, pairs=2000):
@@ -557,6 +676,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--full-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-beam", type=int, default=192)
     ap.add_argument("--ref-queries", type=int, default=200)

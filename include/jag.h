@@ -260,6 +260,114 @@ JAG_API jag_status jag_mlp_train(int32_t n_ladder, float *params, float *adam_m,
 JAG_API jag_status jag_mlp_export(int32_t n_ladder, const float *params, uint16_t *w_bf16, float *b_f32,
                                   void *stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: a device-resident request loop with continuous batching (an
+ * extension of this library; the paper evaluates batches of queries only).
+ *
+ * A persistent kernel keeps one warp per query in flight, like jag_search,
+ * but takes its queries from a ring of requests in mapped host memory as
+ * they arrive: a warp that finishes a query claims the next published one,
+ * whatever request it belongs to, so requests that arrive while others are
+ * running are admitted as soon as warps free up and their work overlaps on
+ * the device.  Each query is answered exactly as jag_search answers it with
+ * the same k, beam, s0, scan_cap, hash_bits and policy (the same routing,
+ * scan and graph search), so a result does not depend on what else is in
+ * flight.  Inputs and outputs stay in pinned host memory that the kernel
+ * reads and writes directly; there is no copy call per request.
+ *
+ * Admission: a request is admitted when a ring slot, room for its inputs and
+ * outputs in the host arena, and room for its boolean filter tables in the
+ * device scratch budget (lut_bytes) are all free; space is returned when its
+ * results are collected by jag_serve_wait.  Every wait of the device loop is
+ * bounded: it exits after idle_exit_s without work (the library starts it
+ * again when work arrives) and on jag_serve_stop.
+ *
+ * One thread may submit while another waits; calls on one server are
+ * serialised internally.
+ * ------------------------------------------------------------------------ */
+typedef struct jag_server jag_server;   /* opaque */
+
+typedef struct jag_serve_params {
+  int32_t k;                   /* answers per query, 1..beam                   */
+  int32_t beam;                /* l_s, k..256                                  */
+  int64_t s0;                  /* as jag_search_args.s0                        */
+  int64_t scan_cap;            /* as jag_search_args.scan_cap                  */
+  int32_t hash_bits;           /* as jag_search_args.hash_bits                 */
+  int32_t max_requests;        /* ring slots (admitted, not yet collected);
+                                  0 = 1024, at most 65536                      */
+  int64_t max_queries;         /* queries admitted at once; 0 = 65536          */
+  int64_t arena_bytes;         /* host arena for inputs / outputs; 0 = enough
+                                  for max_queries queries with 64 bytes of
+                                  truth tables each                            */
+  int64_t lut_bytes;           /* device budget for boolean filter tables
+                                  (8 bytes per truth-table byte); 0 = 16 MiB   */
+  int32_t ctas;                /* persistent CTAs; 0 = as many as are resident */
+  int32_t reserved;            /* 0                                            */
+  double idle_exit_s;          /* device loop exits after this long with no
+                                  work; 0 = 1.0                                */
+  const jag_policy *policy;    /* LEARNED or PLAIN policy, or NULL; its
+                                  forced / features / decisions must be NULL;
+                                  copied at start                              */
+} jag_serve_params;
+
+typedef struct jag_serve_timing {
+  double submit_s;             /* host steady clock at submission (seconds)    */
+  double done_s;               /* host steady clock when completion was seen   */
+  double device_s;             /* device time from the claim of the request's
+                                  first query to the end of its last one       */
+  uint32_t status;             /* bit 2: a query had an invalid filter (its
+                                  answers are padded)                          */
+  uint32_t reserved;
+} jag_serve_timing;
+
+/* Start a server on idx (which must outlive it).  Allocates the ring, the
+ * arena (pinned, mapped) and the device scratch, and launches the loop.
+ * Errors: JAG_EINVAL (bad parameters), JAG_ENOMEM, JAG_ECUDA. */
+JAG_API jag_status jag_serve_start(jag_index *idx, const jag_serve_params *params, jag_server **out);
+
+/* Submit one request of nq >= 1 queries from HOST buffers: queries [nq][d]
+ * fp32, filters [nq], aux: the truth tables the boolean filters point into
+ * (aux_bytes bytes; may be NULL if no filter is boolean).  The inputs are
+ * copied (boolean tables are repacked; aux_off is rewritten in the copy), so
+ * the caller may reuse its buffers on return.  Waits up to timeout_s for
+ * admission: JAG_ETIMEOUT if there was no room in time (nothing is
+ * submitted), JAG_EINVAL if the request could never fit.  *ticket
+ * identifies the request. */
+JAG_API jag_status jag_serve_submit(jag_server *srv, const float *queries, const jag_filter *filters,
+                                    const uint8_t *aux, int64_t aux_bytes, int32_t nq, double timeout_s,
+                                    uint64_t *ticket);
+
+/* Wait up to timeout_s (0: just test) for a request, then copy its answers
+ * to HOST buffers ids [nq][k], dist [nq][k] (either may be NULL) and its
+ * timing to *timing (may be NULL), and release its space.  JAG_ETIMEOUT if
+ * it is not complete in time (the ticket stays valid); JAG_EINVAL for an
+ * unknown ticket. */
+JAG_API jag_status jag_serve_wait(jag_server *srv, uint64_t ticket, int32_t *ids, float *dist,
+                                  jag_serve_timing *timing, double timeout_s);
+
+/* Open-loop driver for measurements: request r, of sizes[r] queries taken
+ * from rows first[r].. of the HOST pools (queries [*][d], filters [*], aux),
+ * is submitted arrival_s[r] seconds after the call starts (arrival_s
+ * non-decreasing), or later when there is no room; completions are
+ * collected as they happen.  Outputs (HOST, each may be NULL): ids / dist
+ * [*][k] at the requests' rows; latency_s[r] = completion seen - scheduled
+ * arrival; device_s[r] as in jag_serve_timing.  Returns when every request
+ * is complete, or JAG_ETIMEOUT after timeout_s in total. */
+JAG_API jag_status jag_serve_replay(jag_server *srv, int64_t n_req, const double *arrival_s, const int32_t *sizes,
+                                    const int64_t *first, const float *queries, const jag_filter *filters,
+                                    const uint8_t *aux, int64_t aux_bytes, int32_t *ids, float *dist,
+                                    double *latency_s, double *device_s, double timeout_s);
+
+/* Counters of a server: launches of the device loop so far, and queries
+ * completed. */
+JAG_API jag_status jag_serve_info(const jag_server *srv, int64_t *launches, int64_t *queries_done);
+
+/* Drain: wait for every admitted request to finish on the device (the loop
+ * then exits), release everything (uncollected results are dropped).  NULL
+ * is allowed.  JAG_ETIMEOUT if the device did not finish within 60 s (the
+ * server is then leaked rather than freed under running work). */
+JAG_API jag_status jag_serve_stop(jag_server *srv);
+
 /* Index facts. */
 typedef struct jag_info {
   int64_t n, d;

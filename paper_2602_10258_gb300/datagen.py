@@ -300,10 +300,11 @@ def make_subset(n=1_000_000, d=100, nq=10_000, seed=0, n_centres=200,
 
 
 def make_mixed(n=1_000_000, d=128, nq=10_000, seed=0, n_centres=100, nbits=32,
-               p_bit=0.3) -> Workload:
+               p_bit=0.3, query_seed=None) -> Workload:
     """Float-range and boolean filters over one point set; the graph is built
     on the float attribute (``dist_a`` = range) -- the boolean column is
-    carried for filtering."""
+    carried for filtering.  query_seed: draw the queries from another seed
+    over the same base set; None = seed."""
     centres = mixture_centres(_rng(seed, 30), n_centres, d)
     x = gaussian_mixture(_rng(seed, 31), n, d, centres)
     af = _rng(seed, 32).random(n, dtype=np.float32)
@@ -311,8 +312,9 @@ def make_mixed(n=1_000_000, d=128, nq=10_000, seed=0, n_centres=100, nbits=32,
     masks = np.zeros(n, dtype=np.uint64)
     for j in range(nbits):
         masks |= (rb.random(n) < p_bit).astype(np.uint64) << np.uint64(j)
-    q = gaussian_mixture(_rng(seed, 34), nq, d, centres)
-    rf = _rng(seed, 35)
+    qs = seed if query_seed is None else query_seed
+    q = gaussian_mixture(_rng(qs, 34), nq, d, centres)
+    rf = _rng(qs, 35)
     is_bool = rf.random(nq) < 0.5
     w = (10.0 ** rf.uniform(-4.0, 0.0, size=nq)).astype(np.float32)
     lo = (rf.random(nq) * (1.0 - w)).astype(np.float32)

@@ -59,6 +59,20 @@ class PolicyStruct(C.Structure):
                 ("decisions", C.c_void_p)]
 
 
+class ServeParams(C.Structure):
+    """Mirror of jag_serve_params."""
+    _fields_ = [("k", C.c_int32), ("beam", C.c_int32), ("s0", C.c_int64), ("scan_cap", C.c_int64),
+                ("hash_bits", C.c_int32), ("max_requests", C.c_int32), ("max_queries", C.c_int64),
+                ("arena_bytes", C.c_int64), ("lut_bytes", C.c_int64), ("ctas", C.c_int32),
+                ("reserved", C.c_int32), ("idle_exit_s", C.c_double), ("policy", C.c_void_p)]
+
+
+class ServeTiming(C.Structure):
+    """Mirror of jag_serve_timing."""
+    _fields_ = [("submit_s", C.c_double), ("done_s", C.c_double), ("device_s", C.c_double),
+                ("status", C.c_uint32), ("reserved", C.c_uint32)]
+
+
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("R", C.c_int32), ("storage", C.c_int32),
                 ("entry", C.c_int64), ("device_bytes", C.c_int64), ("build_seconds", C.c_double),
@@ -67,7 +81,8 @@ class Info(C.Structure):
 
 EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_search_noalloc", "jag_get_info",
             "jag_get_graph", "jag_get_thresholds", "jag_get_stored_rows", "jag_free", "jag_last_error",
-            "jag_version", "jag_mlp_loss_grad", "jag_mlp_train", "jag_mlp_export"]
+            "jag_version", "jag_mlp_loss_grad", "jag_mlp_train", "jag_mlp_export", "jag_serve_start",
+            "jag_serve_submit", "jag_serve_wait", "jag_serve_replay", "jag_serve_info", "jag_serve_stop"]
 
 _lib = None
 _lock = threading.Lock()
@@ -118,6 +133,19 @@ def load(build_if_missing: bool = True):
             L.jag_mlp_train.restype = C.c_int
             L.jag_mlp_export.argtypes = [I32, P, P, P, P]
             L.jag_mlp_export.restype = C.c_int
+            D = C.c_double
+            L.jag_serve_start.argtypes = [P, P, C.POINTER(C.c_void_p)]
+            L.jag_serve_start.restype = C.c_int
+            L.jag_serve_submit.argtypes = [P, P, P, P, I64, I32, D, C.POINTER(C.c_uint64)]
+            L.jag_serve_submit.restype = C.c_int
+            L.jag_serve_wait.argtypes = [P, C.c_uint64, P, P, P, D]
+            L.jag_serve_wait.restype = C.c_int
+            L.jag_serve_replay.argtypes = [P, I64, P, P, P, P, P, P, I64, P, P, P, P, D]
+            L.jag_serve_replay.restype = C.c_int
+            L.jag_serve_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.jag_serve_info.restype = C.c_int
+            L.jag_serve_stop.argtypes = [P]
+            L.jag_serve_stop.restype = C.c_int
             _lib = L
     return _lib
 
@@ -454,3 +482,85 @@ class Trainer:
 def mlp_export(nl, params, w_bf16, b_f32, stream=None):
     _check(load().jag_mlp_export(int(nl), params.data_ptr(), w_bf16.data_ptr(), b_f32.data_ptr(),
                                  _stream_ptr(stream, params.device)))
+
+
+# ---------------------------------------------------------------------------
+# serving: device-resident request loop
+# ---------------------------------------------------------------------------
+
+class Server:
+    """A jag_server on an index: submit requests from host arrays, wait for
+    their answers, or replay an arrival schedule.  Stop (or close) to drain
+    and release it."""
+
+    def __init__(self, index, k, beam, s0=-1, scan_cap=0, hash_bits=0, max_requests=0, max_queries=0,
+                 arena_bytes=0, lut_bytes=0, ctas=0, idle_exit_s=0.0, policy=None):
+        self.index = index
+        self.k = int(k)
+        self.d = index.d
+        p = ServeParams()
+        p.k, p.beam, p.s0, p.scan_cap, p.hash_bits = int(k), int(beam), int(s0), int(scan_cap), int(hash_bits)
+        p.max_requests, p.max_queries, p.arena_bytes = int(max_requests), int(max_queries), int(arena_bytes)
+        p.lut_bytes, p.ctas, p.idle_exit_s = int(lut_bytes), int(ctas), float(idle_exit_s)
+        self._pol = None if policy is None else policy.struct()
+        p.policy = None if self._pol is None else C.addressof(self._pol)
+        self.h = C.c_void_p()
+        _check(load().jag_serve_start(index.h, C.byref(p), C.byref(self.h)))
+        self._nq = {}
+
+    def submit(self, queries, filters, aux=None, timeout_s=10.0):
+        q = np.ascontiguousarray(queries, np.float32)
+        f = np.ascontiguousarray(filters)
+        a = None if aux is None else np.ascontiguousarray(aux, np.uint8)
+        t = C.c_uint64(0)
+        _check(load().jag_serve_submit(self.h, q.ctypes.data, f.ctypes.data, None if a is None else a.ctypes.data,
+                                       0 if a is None else a.nbytes, len(q), float(timeout_s), C.byref(t)))
+        self._nq[t.value] = len(q)
+        return t.value
+
+    def wait(self, ticket, timeout_s=10.0):
+        """(ids [nq][k], dist [nq][k], timing dict) of a submitted request."""
+        nq = self._nq[ticket]
+        ids = np.empty((nq, self.k), np.int32)
+        dist = np.empty((nq, self.k), np.float32)
+        tm = ServeTiming()
+        _check(load().jag_serve_wait(self.h, C.c_uint64(ticket), ids.ctypes.data, dist.ctypes.data, C.byref(tm),
+                                     float(timeout_s)))
+        del self._nq[ticket]
+        return ids, dist, {f: getattr(tm, f) for f, _ in ServeTiming._fields_}
+
+    def replay(self, arrival_s, sizes, first, queries, filters, aux=None, timeout_s=120.0):
+        """Open-loop replay: returns (ids, dist, latency_s [n_req], device_s [n_req])."""
+        arr = np.ascontiguousarray(arrival_s, np.float64)
+        sz = np.ascontiguousarray(sizes, np.int32)
+        fi = np.ascontiguousarray(first, np.int64)
+        q = np.ascontiguousarray(queries, np.float32)
+        f = np.ascontiguousarray(filters)
+        a = None if aux is None else np.ascontiguousarray(aux, np.uint8)
+        ids = np.full((len(q), self.k), -1, np.int32)
+        dist = np.full((len(q), self.k), np.inf, np.float32)
+        lat = np.zeros(len(arr))
+        dev = np.zeros(len(arr))
+        _check(load().jag_serve_replay(self.h, len(arr), arr.ctypes.data, sz.ctypes.data, fi.ctypes.data,
+                                       q.ctypes.data, f.ctypes.data, None if a is None else a.ctypes.data,
+                                       0 if a is None else a.nbytes, ids.ctypes.data, dist.ctypes.data,
+                                       lat.ctypes.data, dev.ctypes.data, float(timeout_s)))
+        return ids, dist, lat, dev
+
+    def info(self):
+        la, qd = C.c_int64(0), C.c_int64(0)
+        _check(load().jag_serve_info(self.h, C.byref(la), C.byref(qd)))
+        return {"launches": la.value, "queries_done": qd.value}
+
+    def stop(self):
+        if self.h:
+            _check(load().jag_serve_stop(self.h))
+            self.h = None
+
+    close = stop
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -61,7 +61,9 @@ def _c_layout(struct, fields):
 @pytest.mark.parametrize("struct,cls", [("jag_build_params", jag.BuildParams),
                                         ("jag_search_args", jag.SearchArgs),
                                         ("jag_info", jag.Info),
-                                        ("jag_policy", jag.PolicyStruct)])
+                                        ("jag_policy", jag.PolicyStruct),
+                                        ("jag_serve_params", jag.ServeParams),
+                                        ("jag_serve_timing", jag.ServeTiming)])
 def test_record_layouts_match_header(struct, cls):
     fields = [f for f, _ in cls._fields_]
     lay = _c_layout(struct, fields)
@@ -98,3 +100,9 @@ def test_null_arguments_rejected_without_gpu(lib):
     step = C.c_int64(0)
     assert lib.jag_mlp_train(9, None, None, None, C.byref(step), None, None, None, 1, 1, 1, 1e-3, 0.0, None,
                              None) == jag.JAG_EINVAL
+    srv = C.c_void_p()
+    assert lib.jag_serve_start(None, None, C.byref(srv)) == jag.JAG_EINVAL
+    t = C.c_uint64(0)
+    assert lib.jag_serve_submit(None, None, None, None, 0, 1, 0.0, C.byref(t)) == jag.JAG_EINVAL
+    assert lib.jag_serve_wait(None, 1, None, None, None, 0.0) == jag.JAG_EINVAL
+    assert lib.jag_serve_stop(None) == jag.JAG_OK
