@@ -73,6 +73,19 @@ def recall_at_k(ids, gt_ids, gt_d, k=K):
     return out
 
 
+def aggregate_timing(total_ms, steps, nq_per_rank, world, device):
+    """Whole-job timing of a replicated run: the slowest rank's time (max over
+    ranks) and the queries of all ranks divided by it."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * nq_per_rank / (ms_per_step / 1000.0)
+
+
 def band_of(sel):
     b = np.full(len(sel), -1)
     for j, (lo, hi, _) in enumerate(BANDS):
@@ -270,13 +283,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     step_ms = np.array([s.elapsed_time(e) for s, e, _, _ in ev])
     kern_ms = np.array([a.elapsed_time(b) for _, _, a, b in ev])
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * nq / (ms_per_step / 1000.0)
+    ms_per_step, value = aggregate_timing(float(step_ms.sum()), args.steps, nq, world, dev)
 
     # per-band QPS at each band's own smallest beam (informational)
     bands_out = {}

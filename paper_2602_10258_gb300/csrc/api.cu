@@ -437,6 +437,7 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   L.rr = L0.rr;
   L.rr_ids = (int32_t *)(base + L0.rr_ids);
   if (a->policy) { L.policy = *a->policy; L.has_policy = 1; }
+  L.fork_scan = 1;
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
   L.ev_end = (cudaEvent_t)a->ev_graph_end;
   L.stream = stream;

@@ -40,6 +40,7 @@ struct SearchLaunch {
   int32_t *rr_ids;         // [nq][rr]
   cudaEvent_t ev_begin, ev_end;
   cudaStream_t stream;
+  int32_t fork_scan;       // run the exact scan on a side stream, concurrently
 };
 
 // Graph-search launch for rows stored in format FMT (search_<fmt>.cu).

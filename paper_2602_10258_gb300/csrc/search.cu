@@ -247,7 +247,7 @@ scan_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
         if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
       }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
       __syncwarp();   // rows[cur] and cids[cur] are reused by round r + 2
     }
     uint64_t *pk = part_key + (qi * ntiles + t) * k;
@@ -306,7 +306,7 @@ merge_scan_kernel(const DevIndex ix, const jag_filter *filters, const QueryPlan 
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -361,7 +361,7 @@ brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fi
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
     int r0;
-    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
   }
   for (int j = lane; j < k; j += 32) {
     pk[j] = j < cnt ? S.bkey[j] : kNoKey;
@@ -390,7 +390,7 @@ merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const 
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -436,7 +436,7 @@ rerank_kernel(DevIndex ix, const float *queries, int d, const QueryPlan *plans, 
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
     int r0;
-    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0);
+    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
 }
@@ -605,6 +605,18 @@ static cudaError_t dispatch_job(const SearchLaunch &L, int P, int CPL, Job job, 
   }
 }
 
+// Per-device stream on which the exact scan runs beside the graph search.
+static cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
 cudaError_t run_search(const SearchLaunch &L) {
   if (L.nq == 0) return cudaSuccess;
   int P, CPL;
@@ -628,16 +640,48 @@ cudaError_t run_search(const SearchLaunch &L) {
                                                                                  L.cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  // The exact scan of the routed queries and the graph search of the others
+  // touch disjoint queries.  The graph search is enqueued first, so that its
+  // persistent CTAs take the SMs; the scan follows on a side stream and fills
+  // the SMs that the graph search's last wave leaves idle; the two join
+  // before the call's work ends.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if (L.s0 > 0 && L.fork_scan) {
+    side = side_stream();
+    if (!side || cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+      side = nullptr;
+    } else if (cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(ev_fork);
+      side = nullptr;
+    } else if ((e = cudaEventRecord(ev_fork, L.stream)) != cudaSuccess) {
+      cudaEventDestroy(ev_fork);
+      cudaEventDestroy(ev_join);
+      return e;
+    }
+  }
   // graph search in the stored format, then the fp32 re-rank when the rows
-  // are BF16 / FP8, then the exact scan of the routed queries
+  // are BF16 / FP8
   switch (L.ix.fmt) {
     case JAG_VEC_F32: e = launch_graph_fmt<JAG_VEC_F32>(L); break;
     case JAG_VEC_BF16: e = launch_graph_fmt<JAG_VEC_BF16>(L); break;
     case JAG_VEC_FP8: e = launch_graph_fmt<JAG_VEC_FP8>(L); break;
-    default: return cudaErrorInvalidValue;
+    default: e = cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess && L.ix.fmt != JAG_VEC_F32) e = dispatch_job(L, P, CPL, kJobRerank, L.k);
+  if (side) {
+    SearchLaunch S = L;
+    S.stream = side;
+    S.ev_begin = S.ev_end = nullptr;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+    if (e == cudaSuccess) e = dispatch_job(S, P, CPL, kJobScan, L.k);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_join, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L.stream, ev_join, 0);
+    cudaEventDestroy(ev_fork);
+    cudaEventDestroy(ev_join);
+    return e;
   }
   if (e != cudaSuccess) return e;
-  if (L.ix.fmt != JAG_VEC_F32 && (e = dispatch_job(L, P, CPL, kJobRerank, L.k)) != cudaSuccess) return e;
   if (L.s0 > 0) return dispatch_job(L, P, CPL, kJobScan, L.k);
   return cudaSuccess;
 }

@@ -112,7 +112,7 @@ __device__ __forceinline__ int list_rank(const uint64_t *bkey, const uint32_t *b
 // the new count; r0 receives the smallest insertion position (cnt if none).
 template <int CAP>
 __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, int cnt, int ls, uint64_t ck,
-                                                uint32_t cv, int &r0) {
+                                                uint32_t cv, int &r0, uint32_t *srank) {
   const int lane = threadIdx.x & 31;
   bool valid = ck != kNoKey;
   r0 = cnt;
@@ -133,15 +133,24 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
     crank += key_less(ok, oi, ck, cv) ? 1 : 0;
   }
   r0 = (int)__reduce_min_sync(kFull, valid ? (unsigned)rank : 0xFFFFFFFFu);
-  // entry j moves right by the number of new keys ranked at or before j;
-  // chunks from the back never overwrite an entry not yet read
+  // the new keys' ranks in L, in the new keys' order (non-decreasing), padded
+  const int nv = __popc(vm);
+  if (valid) srank[crank] = (uint32_t)rank;
+  if (lane >= nv) srank[lane] = 0xFFFFFFFFu;
+  __syncwarp();
+  // entry j moves right by the number of new keys ranked at or before j (a
+  // 5-step search of srank); chunks from the back never overwrite an entry
+  // not yet read
   for (int t = (cnt - r0 + 31) / 32 - 1; t >= 0; --t) {
     const int j = r0 + 32 * t + lane;
     uint64_t ek = 0;
     uint32_t ei = 0;
     if (j < cnt) { ek = bkey[j]; ei = bid[j]; }
-    int sh = 0;
-    for (uint32_t m = vm; m; m &= m - 1) sh += (__shfl_sync(kFull, rank, __ffs(m) - 1) <= j) ? 1 : 0;
+    int sh = srank[31] <= (uint32_t)j ? 32 : 0;
+    if (sh == 0) {
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) sh += (srank[sh + step - 1] <= (uint32_t)j) ? step : 0;
+    }
     __syncwarp();
     if (j < cnt && j + sh < ls) { bkey[j + sh] = ek; bid[j + sh] = ei; }
     __syncwarp();
@@ -485,7 +494,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
         if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
       }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0, S.rank);
       rmin = r0 < rmin ? r0 : rmin;
       if (POL && r0 < pc->k) last_change = st.hops;
     }
