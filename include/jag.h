@@ -106,6 +106,15 @@ typedef struct jag_build_params {
   const int32_t *graph;         /* optional host [n][R] out-lists (-1 padded):
                                    when given, the build is skipped            */
   int64_t entry;                /* entry vertex when graph is given            */
+  int32_t n_weights;            /* Weight-JAG (the weighted variant of Sec. 3):
+                                   0 = Threshold-JAG; 1..8 = build with the
+                                   comparators D_A^w = w dist_A + dist, one per
+                                   weight w = weight_mult[i] * h_p, with
+                                   h_p = sigma / sigma_A of point p over the
+                                   threshold sample (implementation-details
+                                   appendix); the thresholds are then unused  */
+  int32_t reserved;             /* 0                                           */
+  double weight_mult[8];        /* multipliers c_i >= 0 of h (e.g. 0, 1, 10)   */
 } jag_build_params;
 
 typedef struct jag_index jag_index;   /* opaque */
@@ -375,7 +384,8 @@ typedef struct jag_info {
   int64_t entry;
   int64_t device_bytes;         /* bytes the index holds on the device         */
   double build_seconds;         /* wall time of the GPU build, 0 if uploaded   */
-  int32_t n_thresholds, dist_a;
+  int32_t n_thresholds, dist_a;  /* n_thresholds: |T|, or |W| of a Weight-JAG build */
+  int32_t weighted, reserved;      /* 1 for a Weight-JAG build                   */
 } jag_info;
 JAG_API jag_status jag_get_info(const jag_index *idx, jag_info *out);
 
@@ -383,8 +393,9 @@ JAG_API jag_status jag_get_info(const jag_index *idx, jag_info *out);
 JAG_API jag_status jag_get_graph(const jag_index *idx, int32_t *host_out);
 
 /* Copy the per-point thresholds [n][n_thresholds] (dist_A in the ordered
- * 32-bit form: integer value, or float bit pattern) to host memory;
- * JAG_EINVAL if the graph was uploaded rather than built. */
+ * 32-bit form: integer value, or float bit pattern) to host memory -- for a
+ * Weight-JAG build, the per-point weights [n][n_weights] as fp32 bit
+ * patterns; JAG_EINVAL if the graph was uploaded rather than built. */
 JAG_API jag_status jag_get_thresholds(const jag_index *idx, uint32_t *host_out);
 
 /* Copy the stored BF16 / FP8 rows [n][row_bytes] (row_bytes = d * element

@@ -398,17 +398,31 @@ typedef struct {
   /* build comparator D_A^t */
   int64_t p;                /* base point being inserted, or -1 for a query    */
   uint32_t t;
+  /* Weight-JAG build comparator D_A^w = w dist_A + dist (a scalar key) */
+  int weighted;
+  float w;
 } comparator_t;
 
 /* Vector distance of the comparator: the build compares fp32 rows; a query
  * compares the index's stored rows (fp32, or BF16 / FP8 before re-ranking). */
+/* dist_A(a_i, a_j) as a real number: the float range distance is the fp32
+ * value; the integer distances are converted to fp32 (round to nearest). */
+float orc_dist_A_value(const orc_index *ix, int64_t i, int64_t j) {
+  const uint32_t da = orc_dist_A(ix, i, j);
+  return ix->dist_a == K_RANGE_F32 ? u2f(da) : (float)da;
+}
+
 static inline float cmp_dist(const comparator_t *c, int64_t u) {
-  if (c->p >= 0) return orc_dist_canon(c->xq, c->ix->x + u * c->ix->d, c->ix->d);
+  if (c->p >= 0) {
+    const float d = orc_dist_canon(c->xq, c->ix->x + u * c->ix->d, c->ix->d);
+    /* Weight-JAG: D_A^w(p, u) = w * dist_A(a_p, a_u) + dist(x_p, x_u), one fp32 fma */
+    return c->weighted ? fmaf(c->w, orc_dist_A_value(c->ix, c->p, u), d) : d;
+  }
   return search_dist(c->ix, c->xq, u);
 }
 
 static inline uint32_t first_key(const comparator_t *c, int64_t u) {
-  if (c->p >= 0) return orc_capped(c->ix->dist_a, orc_dist_A(c->ix, c->p, u), c->t);
+  if (c->p >= 0) return c->weighted ? 0u : orc_capped(c->ix->dist_a, orc_dist_A(c->ix, c->p, u), c->t);
   return orc_dist_F(c->ix, u, c->f, c->lut);
 }
 
@@ -885,7 +899,7 @@ static void query_range(void *ctx, int64_t lo, int64_t hi, int tid) {
       bf_one(&b, qi);
       if (cn) { cn[0] = 0; cn[1] = 0; cn[2] = 0; cn[3] = 1; }
     } else {
-      comparator_t cmp = {ix, c->q + qi * ix->d, f, lut, -1, 0};
+      comparator_t cmp = {ix, c->q + qi * ix->d, f, lut, -1, 0, 0, 0.0f};
       int m = 0;
       counters_t cnt = {0, 0, 0};
       if (c->pol) {
@@ -1063,40 +1077,59 @@ void orc_thresholds(const orc_index *ix, const int32_t *pct, int nT, int S, uint
   parallel_for(ix->n, nthreads, thr_range, &c);
 }
 
+/* One candidate of a prune ranking: (k1, key, id) lexicographic; idx is the
+ * candidate's position in the caller's arrays. */
+typedef struct { uint32_t k1; float key; int32_t id; int32_t idx; } pentry_t;
+
+static int pentry_cmp(const void *pa, const void *pb) {
+  const pentry_t *a = (const pentry_t *)pa, *b = (const pentry_t *)pb;
+  if (a->k1 != b->k1) return a->k1 < b->k1 ? -1 : 1;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->id < b->id ? -1 : a->id > b->id;
+}
+
 /* JointRobustPrune (Algorithm 4).  cand[0..nc) are distinct candidate ids
- * (p excluded) with dpc[i] = dist(p, cand[i]).  For each threshold t of p in
- * order: rank the candidates by D_A^t(p, .) = (capped dist_A, dist, id); walk
- * them, keeping v if it was already chosen for an earlier threshold, else if
- * alpha * dist(u, v) > dist(p, v) for every u kept for this threshold so far
+ * (p excluded) with dpc[i] = dist(p, cand[i]).  For each parameter of p in
+ * order -- a threshold t (rank by D_A^t(p, .) = (capped dist_A, dist, id)) or,
+ * with weighted != 0, a weight w given as fp32 bits (rank by D_A^w(p, .) =
+ * (w dist_A + dist, id), the Weight-JAG comparator) -- walk the candidates,
+ * keeping v if it was already chosen for an earlier parameter, else if
+ * alpha * dist(u, v) > dist(p, v) for every u kept for this parameter so far
  * (squared distances: alpha^2 d2(u,v) > d2(p,v), alpha^2 rounded to fp32 and
  * the product rounded to fp32); stop once the bucket holds 0.9 R / |T|
  * members.  The union of the buckets, in the order first chosen, is the new
  * out-list (at most R).  Returns its length. */
 static int joint_prune(const orc_index *ix, int64_t p, const int32_t *cand, const float *dpc, int nc,
-                       const uint32_t *T, int nT, float alpha2, int32_t *out) {
+                       const uint32_t *T, int nT, float alpha2, int weighted, int32_t *out) {
   int R = ix->R;
-  entry_t *ord = (entry_t *)malloc(sizeof(entry_t) * (size_t)(nc > 0 ? nc : 1));
+  pentry_t *ord = (pentry_t *)malloc(sizeof(pentry_t) * (size_t)(nc > 0 ? nc : 1));
   int32_t *chosen = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc + 1));
   int32_t *bucket = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc + 1));
   int nchosen = 0;
   for (int ti = 0; ti < nT; ++ti) {
     for (int i = 0; i < nc; ++i) {
-      ord[i].k1 = orc_capped(ix->dist_a, orc_dist_A(ix, p, cand[i]), T[ti]);
-      ord[i].dist = dpc[i];
+      if (weighted) {
+        ord[i].k1 = 0;
+        ord[i].key = fmaf(u2f(T[ti]), orc_dist_A_value(ix, p, cand[i]), dpc[i]);
+      } else {
+        ord[i].k1 = orc_capped(ix->dist_a, orc_dist_A(ix, p, cand[i]), T[ti]);
+        ord[i].key = dpc[i];
+      }
       ord[i].id = cand[i];
-      ord[i].expanded = 0;
+      ord[i].idx = i;
     }
-    qsort(ord, (size_t)nc, sizeof(entry_t), entry_cmp);
+    qsort(ord, (size_t)nc, sizeof(pentry_t), pentry_cmp);
     int nb = 0;
     for (int i = 0; i < nc; ++i) {
       int32_t v = ord[i].id;
+      const float dpv = dpc[ord[i].idx];
       int carried = 0;
       for (int j = 0; j < nchosen; ++j) if (chosen[j] == v) { carried = 1; break; }
       int keep = 1;
       if (!carried) {
         for (int j = 0; j < nb; ++j) {
           float duv = orc_dist_canon(ix->x + (int64_t)bucket[j] * ix->d, ix->x + (int64_t)v * ix->d, ix->d);
-          if (!(alpha2 * duv > ord[i].dist)) { keep = 0; break; }
+          if (!(alpha2 * duv > dpv)) { keep = 0; break; }
         }
       }
       if (keep) bucket[nb++] = v;
@@ -1117,7 +1150,7 @@ static int joint_prune(const orc_index *ix, int64_t p, const int32_t *cand, cons
 typedef struct {
   const orc_index *ix;
   const int64_t *batch; int64_t nb;
-  const uint32_t *thr; int nT; int lb; float alpha2;
+  const uint32_t *thr; int nT; int lb; float alpha2; int weighted;
   int32_t *newrows;       /* [nb][R] */
   int64_t *visited_total; /* statistics */
 } ins_ctx;
@@ -1142,7 +1175,8 @@ static void insert_range(void *ctx, int64_t lo, int64_t hi, int tid) {
     int64_t p = c->batch[bi];
     int nc = 0;
     for (int ti = 0; ti < c->nT; ++ti) {
-      comparator_t cmp = {ix, ix->x + p * ix->d, NULL, NULL, p, c->thr[p * c->nT + ti]};
+      const uint32_t par = c->thr[p * c->nT + ti];
+      comparator_t cmp = {ix, ix->x + p * ix->d, NULL, NULL, p, par, c->weighted, u2f(par)};
       counters_t cnt = {0, 0, 0};
       int len = 0; int64_t nt = 0, nv = 0;
       greedy_direct(&cmp, lb, L, &len, seen, touched, &nt, vis, vcap, &nv, &cnt);
@@ -1152,11 +1186,14 @@ static void insert_range(void *ctx, int64_t lo, int64_t hi, int tid) {
         int32_t v = vis[i].id;
         if (inV[v]) continue;
         inV[v] = 1;
-        cand[nc] = v; dpc[nc] = vis[i].dist; ++nc;
+        /* the list holds D_A^w for Weight-JAG: the prune needs dist(p, v) */
+        cand[nc] = v;
+        dpc[nc] = c->weighted ? orc_dist_canon(ix->x + p * ix->d, ix->x + (int64_t)v * ix->d, ix->d) : vis[i].dist;
+        ++nc;
       }
     }
     for (int i = 0; i < nc; ++i) inV[cand[i]] = 0;
-    joint_prune(ix, p, cand, dpc, nc, c->thr + p * c->nT, c->nT, c->alpha2, c->newrows + bi * ix->R);
+    joint_prune(ix, p, cand, dpc, nc, c->thr + p * c->nT, c->nT, c->alpha2, c->weighted, c->newrows + bi * ix->R);
   }
   free(L); free(vis); free(cand); free(dpc); free(seen); free(inV); free(touched);
 }
@@ -1170,7 +1207,7 @@ static int edge_cmp(const void *a, const void *b) {
 
 typedef struct {
   const orc_index *ix; const edge_t *edges; const int64_t *gstart; int64_t ngroups;
-  const uint32_t *thr; int nT; float alpha2;
+  const uint32_t *thr; int nT; float alpha2; int weighted;
 } back_ctx;
 
 /* Insert, second half: add p to N_out(v) for every chosen v; a list that
@@ -1201,7 +1238,7 @@ static void back_range(void *ctx, int64_t lo, int64_t hi, int tid) {
       float *dvc = (float *)malloc(sizeof(float) * (size_t)nc);
       for (int i = 0; i < nc; ++i)
         dvc[i] = orc_dist_canon(ix->x + v * ix->d, ix->x + (int64_t)cand[i] * ix->d, ix->d);
-      joint_prune(ix, v, cand, dvc, nc, c->thr + v * c->nT, c->nT, c->alpha2, row);
+      joint_prune(ix, v, cand, dvc, nc, c->thr + v * c->nT, c->nT, c->alpha2, c->weighted, row);
       free(dvc);
     }
     free(cand);
@@ -1215,7 +1252,8 @@ static void back_range(void *ctx, int64_t lo, int64_t hi, int tid) {
  * the batch are set, then the back-edges are applied.  thr: [n][nT] per-point
  * thresholds from orc_thresholds().  The result does not depend on
  * nthreads.  Returns 0 on success. */
-int orc_build(orc_index *ix, const uint32_t *thr, int nT, int lb, float alpha2, int nthreads) {
+static int build_graph(orc_index *ix, const uint32_t *thr, int nT, int lb, float alpha2, int weighted,
+                       int nthreads) {
   int64_t n = ix->n;
   int R = ix->R;
   for (int64_t i = 0; i < n * R; ++i) ix->graph[i] = -1;
@@ -1233,7 +1271,7 @@ int orc_build(orc_index *ix, const uint32_t *thr, int nT, int lb, float alpha2, 
     int64_t nb = inserted < cap ? inserted : cap;
     if (nb > n - pos) nb = n - pos;
     const int64_t *batch = order + pos;
-    ins_ctx ic = {ix, batch, nb, thr, nT, lb, alpha2, newrows, NULL};
+    ins_ctx ic = {ix, batch, nb, thr, nT, lb, alpha2, weighted, newrows, NULL};
     parallel_for(nb, nthreads, insert_range, &ic);
     int64_t ne = 0;
     for (int64_t bi = 0; bi < nb; ++bi) {
@@ -1250,7 +1288,7 @@ int orc_build(orc_index *ix, const uint32_t *thr, int nT, int lb, float alpha2, 
     for (int64_t i = 0; i < ne; ++i)
       if (i == 0 || edges[i].target != edges[i - 1].target) gstart[ng++] = i;
     gstart[ng] = ne;
-    back_ctx bc = {ix, edges, gstart, ng, thr, nT, alpha2};
+    back_ctx bc = {ix, edges, gstart, ng, thr, nT, alpha2, weighted};
     parallel_for(ng, nthreads, back_range, &bc);
     pos += nb;
     inserted += nb;
@@ -1259,10 +1297,72 @@ int orc_build(orc_index *ix, const uint32_t *thr, int nT, int lb, float alpha2, 
   return 0;
 }
 
+int orc_build(orc_index *ix, const uint32_t *thr, int nT, int lb, float alpha2, int nthreads) {
+  return build_graph(ix, thr, nT, lb, alpha2, 0, nthreads);
+}
+
+/* Weight-JAG build (the weighted variant of Sec. 3): Insert and
+ * JointRobustPrune iterate over each point's weights w (fp32 values, [n][nW])
+ * with the comparator D_A^w; the query path is unchanged. */
+int orc_build_weighted(orc_index *ix, const float *w, int nW, int lb, float alpha2, int nthreads) {
+  return build_graph(ix, (const uint32_t *)w, nW, lb, alpha2, 1, nthreads);
+}
+
 /* JointRobustPrune exposed for tests: cand/dpc as in joint_prune. */
 int orc_joint_prune(const orc_index *ix, int64_t p, const int32_t *cand, const float *dpc, int nc,
                     const uint32_t *T, int nT, float alpha2, int32_t *out) {
-  return joint_prune(ix, p, cand, dpc, nc, T, nT, alpha2, out);
+  return joint_prune(ix, p, cand, dpc, nc, T, nT, alpha2, 0, out);
+}
+
+/* Weighted JointRobustPrune exposed for tests: W holds fp32 weights. */
+int orc_joint_prune_weighted(const orc_index *ix, int64_t p, const int32_t *cand, const float *dpc, int nc,
+                             const float *W, int nW, float alpha2, int32_t *out) {
+  return joint_prune(ix, p, cand, dpc, nc, (const uint32_t *)W, nW, alpha2, 1, out);
+}
+
+/* Per-point weight scale of Weight-JAG (implementation-details appendix):
+ * over the same sample of S points v as the thresholds, h = sigma / sigma_A
+ * with sigma the standard deviation of dist(x_p, x_v) and sigma_A that of
+ * dist_A(a_p, a_v) (population deviations, fp64, sums taken in sample
+ * order; h = 0 if sigma_A = 0).  The weights of p are w_i = fp32(c_i h). */
+typedef struct {
+  const orc_index *ix; const double *mult; int nW; int S; uint64_t seed; float *out; double *h;
+} wgt_ctx;
+
+static void wgt_range(void *ctx, int64_t lo, int64_t hi, int tid) {
+  (void)tid;
+  const wgt_ctx *c = (const wgt_ctx *)ctx;
+  const orc_index *ix = c->ix;
+  int64_t S = ix->n - 1 < c->S ? ix->n - 1 : c->S;
+  double *a = (double *)malloc(sizeof(double) * (size_t)(S > 0 ? S : 1));
+  double *d = (double *)malloc(sizeof(double) * (size_t)(S > 0 ? S : 1));
+  for (int64_t p = lo; p < hi; ++p) {
+    for (int64_t i = 0; i < S; ++i) {
+      const int64_t v = sample_id(c->seed, ix->n, p, i);
+      a[i] = (double)orc_dist_A_value(ix, p, v);
+      d[i] = (double)orc_dist_canon(ix->x + p * ix->d, ix->x + v * ix->d, ix->d);
+    }
+    double ma = 0.0, md = 0.0, va = 0.0, vd = 0.0;
+    for (int64_t i = 0; i < S; ++i) { ma += a[i]; md += d[i]; }
+    if (S > 0) { ma /= (double)S; md /= (double)S; }
+    for (int64_t i = 0; i < S; ++i) {
+      const double ta = a[i] - ma, td = d[i] - md;
+      va += ta * ta;
+      vd += td * td;
+    }
+    if (S > 0) { va /= (double)S; vd /= (double)S; }
+    const double sa = sqrt(va), sd = sqrt(vd);
+    const double h = sa > 0.0 ? sd / sa : 0.0;
+    if (c->h) c->h[p] = h;
+    for (int i = 0; i < c->nW; ++i) c->out[p * c->nW + i] = (float)(c->mult[i] * h);
+  }
+  free(a); free(d);
+}
+
+void orc_weights(const orc_index *ix, const double *mult, int nW, int S, uint64_t seed, float *out, double *h,
+                 int nthreads) {
+  wgt_ctx c = {ix, mult, nW, S, seed, out, h};
+  parallel_for(ix->n, nthreads, wgt_range, &c);
 }
 
 /* Single GreedySearch with D_A^t from base point p (as in Insert); writes the

@@ -65,6 +65,10 @@ def lib():
                 "orc_sm64": (U64, [U64, U64]),
                 "orc_thresholds": (None, [P, P, I32, I32, U64, P, I32]),
                 "orc_build": (I32, [P, P, I32, I32, F32, I32]),
+                "orc_build_weighted": (I32, [P, P, I32, I32, F32, I32]),
+                "orc_joint_prune_weighted": (I32, [P, I64, P, P, I32, P, I32, F32, P]),
+                "orc_weights": (None, [P, P, I32, I32, U64, P, P, I32]),
+                "orc_dist_A_value": (F32, [P, I64, I64]),
                 "orc_joint_prune": (I32, [P, I64, P, P, I32, P, I32, F32, P]),
                 "orc_build_search": (I64, [P, I64, C.c_uint32, I32, P, P, I64]),
                 "orc_dist_F_batch": (None, [P, P, P, P, I64, P]),
@@ -268,6 +272,41 @@ def build(ix: Index, pct=(100, 1, 0), lb=64, alpha=1.2, S=500, seed=0, nthreads=
     if rc:
         raise RuntimeError("oracle build failed")
     return thr
+
+
+def weights(ix: Index, mult=(0, 1, 10), S=500, seed=0, nthreads=None):
+    """Weight-JAG weights: (w [n][len(mult)] float32 = fp32(mult_i * h_p),
+    h [n] float64) with h_p = sigma / sigma_A over the threshold sample."""
+    mult = np.asarray(mult, np.float64)
+    out = np.empty((ix.n, len(mult)), np.float32)
+    h = np.empty(ix.n, np.float64)
+    lib().orc_weights(ix.ref(), _p(mult), len(mult), S, seed, _p(out), _p(h), nthreads or default_threads())
+    return out, h
+
+
+def build_weighted(ix: Index, mult=(0, 1, 10), lb=64, alpha=1.2, S=500, seed=0, nthreads=None):
+    """Weight-JAG build; fills ix.graph and ix.entry, returns (weights, h)."""
+    ix.entry = medoid(ix.x)
+    w, h = weights(ix, mult, S, seed, nthreads)
+    rc = lib().orc_build_weighted(ix.ref(), _p(w), w.shape[1], int(lb), alpha2_of(alpha),
+                                  nthreads or default_threads())
+    if rc:
+        raise RuntimeError("oracle build failed")
+    return w, h
+
+
+def joint_prune_weighted(ix: Index, p, cand, dpc, W, alpha=1.2):
+    cand = _c(cand, np.int32)
+    dpc = _c(dpc, np.float32)
+    W = _c(W, np.float32)
+    out = np.empty(ix.R, np.int32)
+    m = lib().orc_joint_prune_weighted(ix.ref(), int(p), _p(cand), _p(dpc), len(cand), _p(W), len(W),
+                                       alpha2_of(alpha), _p(out))
+    return out[:m]
+
+
+def dist_A_value(ix: Index, i, j):
+    return float(lib().orc_dist_A_value(ix.ref(), int(i), int(j)))
 
 
 def joint_prune(ix: Index, p, cand, dpc, T, alpha=1.2):

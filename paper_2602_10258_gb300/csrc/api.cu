@@ -74,7 +74,7 @@ struct jag_index {
   int device = 0;
   jag::DevIndex ix{};
   int64_t n = 0, d = 0;
-  int32_t R = 0, storage = JAG_VEC_F32, nT = 0, dist_a = 0;
+  int32_t R = 0, storage = JAG_VEC_F32, nT = 0, dist_a = 0, weighted = 0;
   std::vector<void *> allocs;
   size_t device_bytes = 0;
   double build_seconds = 0.0;
@@ -222,9 +222,17 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
   if (!prebuilt) {
     if (p->l_b < 1 || p->l_b > 256) return fail(JAG_EINVAL, "l_b must be in [1, 256]");
     if (!(p->alpha >= 1.0f) || !std::isfinite(p->alpha)) return fail(JAG_EINVAL, "alpha must be finite and >= 1");
-    if (p->n_thresholds < 1 || p->n_thresholds > 4) return fail(JAG_EINVAL, "n_thresholds must be in [1, 4]");
-    for (int i = 0; i < p->n_thresholds; ++i)
-      if (p->threshold_pct[i] < 0 || p->threshold_pct[i] > 100) return fail(JAG_EINVAL, "threshold_pct out of [0,100]");
+    if (p->n_weights < 0 || p->n_weights > 8) return fail(JAG_EINVAL, "n_weights must be in [0, 8]");
+    if (p->n_weights > 0) {
+      for (int i = 0; i < p->n_weights; ++i)
+        if (!(p->weight_mult[i] >= 0.0) || !std::isfinite(p->weight_mult[i]))
+          return fail(JAG_EINVAL, "weight_mult must be finite and >= 0");
+    } else {
+      if (p->n_thresholds < 1 || p->n_thresholds > 4) return fail(JAG_EINVAL, "n_thresholds must be in [1, 4]");
+      for (int i = 0; i < p->n_thresholds; ++i)
+        if (p->threshold_pct[i] < 0 || p->threshold_pct[i] > 100)
+          return fail(JAG_EINVAL, "threshold_pct out of [0,100]");
+    }
     if (p->sample_size < 1 || p->sample_size > 1024) return fail(JAG_EINVAL, "sample_size must be in [1, 1024]");
     switch (p->dist_a) {
       case JAG_F_LABEL: case JAG_F_RANGE_I32:
@@ -321,14 +329,17 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
             "copy graph");
     ix.entry = (int32_t)p->entry;
   } else {
-    I->nT = p->n_thresholds;
+    I->weighted = p->n_weights > 0 ? 1 : 0;
+    I->nT = I->weighted ? p->n_weights : p->n_thresholds;
     API_TRY(I->alloc((void **)&I->thr, sizeof(uint32_t) * (size_t)(n * I->nT)), "allocate thresholds");
     jag::BuildLaunch B{};
     B.ix = ix;
     B.graph = I->graph;
     B.thr = I->thr;
     B.nT = I->nT;
-    for (int i = 0; i < 4; ++i) B.pct[i] = i < I->nT ? p->threshold_pct[i] : 0;
+    B.weighted = I->weighted;
+    for (int i = 0; i < 8; ++i) B.mult[i] = i < p->n_weights ? p->weight_mult[i] : 0.0;
+    for (int i = 0; i < 4; ++i) B.pct[i] = !I->weighted && i < I->nT ? p->threshold_pct[i] : 0;
     B.sample = p->sample_size;
     B.seed = p->seed;
     B.lb = p->l_b;
@@ -370,6 +381,7 @@ jag_status jag_get_info(const jag_index *idx, jag_info *out) {
   out->n = idx->n; out->d = idx->d; out->R = idx->R; out->storage = idx->storage;
   out->entry = idx->ix.entry; out->device_bytes = (int64_t)idx->device_bytes;
   out->build_seconds = idx->build_seconds; out->n_thresholds = idx->nT; out->dist_a = idx->dist_a;
+  out->weighted = idx->weighted; out->reserved = 0;
   return JAG_OK;
 }
 

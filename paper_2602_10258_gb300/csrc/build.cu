@@ -122,6 +122,58 @@ thresholds_kernel(DevIndex ix, int S, uint64_t seed, int nT, Pct pct, uint32_t *
   }
 }
 
+// Weight-JAG weights (implementation-details appendix): over the threshold
+// sample of S points v, h = sigma / sigma_A with sigma the population standard
+// deviation of dist(x_p, x_v) (canonical fp32 distances) and sigma_A that of
+// dist_A(a_p, a_v) as a real number; sums in fp64, in sample order, by one
+// lane (the order fixes the rounding); h = 0 if sigma_A = 0.  The weights
+// of p are w_i = fp32(c_i h).
+struct Mult { double v[8]; };
+constexpr int kWgtWarps = 4;
+
+template <int P, int CPL>
+__global__ void __launch_bounds__(kWgtWarps * 32)
+weights_kernel(DevIndex ix, int S, uint64_t seed, int nW, Mult mult, uint32_t *wout) {
+  __shared__ float sa[kWgtWarps][kMaxSample], sd[kWgtWarps][kMaxSample];
+  __shared__ uint32_t sid[kWgtWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t Ss = ix.n - 1 < S ? ix.n - 1 : S;
+  for (int64_t p = (int64_t)blockIdx.x * kWgtWarps + warp; p < ix.n; p += (int64_t)gridDim.x * kWgtWarps) {
+    QChunks<CPL, JAG_VEC_F32> q;
+    load_point<P, CPL>(ix.x + p * ix.xs, (int)ix.xs, q);
+    for (int64_t i0 = 0; i0 < Ss; i0 += 32) {
+      const int nc = (int)min64(32, Ss - i0);
+      if (lane < nc) {
+        const int64_t i = i0 + lane;
+        const uint64_t r = sm64(seed, ((uint64_t)p << 20) | (uint64_t)i) % (uint64_t)(ix.n - 1);
+        const int64_t o = (int64_t)r < p ? (int64_t)r : (int64_t)r + 1;
+        sid[warp][lane] = (uint32_t)o;
+        const uint32_t da = attribute_distance(ix, p, o);
+        sa[warp][i] = ix.dist_a == JAG_F_RANGE_F32 ? u2f(da) : __uint2float_rn(da);
+      }
+      __syncwarp();
+      const float dist = candidate_distances<P, CPL>(ix, q, sid[warp], nc);
+      if (lane < nc) sd[warp][i0 + lane] = dist;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      double ma = 0.0, md = 0.0, va = 0.0, vd = 0.0;
+      for (int64_t i = 0; i < Ss; ++i) { ma = __dadd_rn(ma, (double)sa[warp][i]); md = __dadd_rn(md, (double)sd[warp][i]); }
+      if (Ss > 0) { ma = __ddiv_rn(ma, (double)Ss); md = __ddiv_rn(md, (double)Ss); }
+      for (int64_t i = 0; i < Ss; ++i) {
+        const double ta = __dsub_rn((double)sa[warp][i], ma), td = __dsub_rn((double)sd[warp][i], md);
+        va = __dadd_rn(va, __dmul_rn(ta, ta));
+        vd = __dadd_rn(vd, __dmul_rn(td, td));
+      }
+      if (Ss > 0) { va = __ddiv_rn(va, (double)Ss); vd = __ddiv_rn(vd, (double)Ss); }
+      const double s_a = __dsqrt_rn(va), s_d = __dsqrt_rn(vd);
+      const double h = s_a > 0.0 ? __ddiv_rn(s_d, s_a) : 0.0;
+      for (int j = 0; j < nW; ++j) wout[p * nW + j] = f2u(__double2float_rn(__dmul_rn(mult.v[j], h)));
+    }
+    __syncwarp();
+  }
+}
+
 // Column sums in index order (fp64), one thread per coordinate.
 __global__ void centroid_kernel(DevIndex ix, double *c) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,8 +210,8 @@ __global__ void medoid_kernel(DevIndex ix, const double *c, unsigned long long *
 
 template <int CAP, int P, int CPL>
 __global__ void __launch_bounds__(kSearchWarps * 32)
-build_search_kernel(DevIndex ix, int64_t pos0, int64_t nb, int nT, const uint32_t *thr, int lb, int hbits,
-                    uint32_t *vis_ids, float *vis_d, int32_t *vis_n, int vcap, unsigned long long *work,
+build_search_kernel(DevIndex ix, int64_t pos0, int64_t nb, int nT, const uint32_t *thr, int weighted, int lb,
+                    int hbits, uint32_t *vis_ids, float *vis_d, int32_t *vis_n, int vcap, unsigned long long *work,
                     uint32_t *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -175,10 +227,15 @@ build_search_kernel(DevIndex ix, int64_t pos0, int64_t nb, int nT, const uint32_
     const int64_t p = order_id(pos0 + bi, ix.entry);
     QChunks<CPL, JAG_VEC_F32> q;
     load_point<P, CPL>(ix.x + p * ix.xs, (int)ix.xs, q);
-    const BuildKey key{p, thr[p * nT + ti]};
     VisitSink sink{vis_ids + it * vcap, vis_d + it * vcap, vcap, 0};
     SearchStats st;
-    greedy_search<CAP, P, CPL, JAG_VEC_F32>(ix, key, q, lb, hbits, S, sink, st);
+    if (weighted) {
+      const WeightKey key{p, u2f(thr[p * nT + ti])};
+      greedy_search<CAP, P, CPL, JAG_VEC_F32>(ix, key, q, lb, hbits, S, sink, st);
+    } else {
+      const BuildKey key{p, thr[p * nT + ti]};
+      greedy_search<CAP, P, CPL, JAG_VEC_F32>(ix, key, q, lb, hbits, S, sink, st);
+    }
     if (lane == 0) {
       vis_n[it] = sink.n;
       if (sink.n > vcap) atomicOr(status, kErrVisitedOverflow);
@@ -239,20 +296,42 @@ __device__ __forceinline__ bool in_list(const uint32_t *list, int n, uint32_t v)
 
 // JointRobustPrune for base point p over candidates S.cid/S.cdist[0..nc).
 // Writes the new out-list (-1 padded) to row.
+//
+// Weight-JAG (weighted != 0): T holds fp32 weights w and the ranking is by
+// D_A^w(p, v) = fma(w, dist_A, dist(p, v)), then id.  The candidates are first
+// put in id order, so that a candidate's index breaks ties like its id, and
+// the ranking sorts indices; dist(p, v) for the alpha test comes from cdist.
 template <int P, int CPL>
 __device__ void joint_prune(const DevIndex &ix, int64_t p, const PruneSmem &S, int nc, int cmax,
-                            const uint32_t *T, int nT, float alpha2, int32_t *row) {
+                            const uint32_t *T, int nT, float alpha2, int weighted, int32_t *row) {
   const int lane = threadIdx.x & 31;
   const int R = ix.R;
   const int M = next_pow2(nc > 0 ? nc : 1);
   int nchosen = 0;
+  if (weighted) {
+    for (int i = lane; i < M; i += 32) {
+      S.skey[i] = i < nc ? (uint64_t)S.cid[i] : kNoKey;
+      S.sid[i] = i < nc ? f2u(S.cdist[i]) : kEmptySlot;
+    }
+    __syncwarp();
+    warp_sort_smem(S.skey, S.sid, M);
+    for (int i = lane; i < nc; i += 32) { S.cid[i] = (uint32_t)S.skey[i]; S.cdist[i] = u2f(S.sid[i]); }
+    __syncwarp();
+  }
   for (int ti = 0; ti < nT; ++ti) {
     const uint32_t t = T[ti];
     for (int i = lane; i < M; i += 32) {
       if (i < nc) {
         const uint32_t c = S.cid[i];
-        S.skey[i] = make_key(capped_distance(ix.dist_a, attribute_distance(ix, p, c), t), S.cdist[i]);
-        S.sid[i] = c;
+        if (weighted) {
+          const uint32_t da = attribute_distance(ix, p, c);
+          const float a = ix.dist_a == JAG_F_RANGE_F32 ? u2f(da) : __uint2float_rn(da);
+          S.skey[i] = make_key(0u, __fmaf_rn(u2f(t), a, S.cdist[i]));
+          S.sid[i] = (uint32_t)i;
+        } else {
+          S.skey[i] = make_key(capped_distance(ix.dist_a, attribute_distance(ix, p, c), t), S.cdist[i]);
+          S.sid[i] = c;
+        }
       } else {
         S.skey[i] = kNoKey;
         S.sid[i] = kEmptySlot;
@@ -262,8 +341,8 @@ __device__ void joint_prune(const DevIndex &ix, int64_t p, const PruneSmem &S, i
     warp_sort_smem(S.skey, S.sid, M);
     int nb = 0;
     for (int i = 0; i < nc; ++i) {
-      const uint32_t v = S.sid[i];
-      const float dpv = u2f((uint32_t)S.skey[i]);
+      const uint32_t v = weighted ? S.cid[S.sid[i]] : S.sid[i];
+      const float dpv = weighted ? S.cdist[S.sid[i]] : u2f((uint32_t)S.skey[i]);
       bool keep = true;
       if (!in_list(S.chosen, nchosen, v) && nb > 0) {
         QChunks<CPL, JAG_VEC_F32> xv;
@@ -301,7 +380,8 @@ __device__ void joint_prune(const DevIndex &ix, int64_t p, const PruneSmem &S, i
 template <int P, int CPL>
 __global__ void __launch_bounds__(kPruneWarps * 32)
 prune_insert_kernel(DevIndex ix, int32_t *graph, int64_t pos0, int64_t nb, int nT, const uint32_t *thr,
-                    float alpha2, const uint32_t *vis_ids, const float *vis_d, const int32_t *vis_n, int vcap,
+                    int weighted, float alpha2, const uint32_t *vis_ids, const float *vis_d, const int32_t *vis_n,
+                    int vcap,
                     int cmax_s, int cmax_g, uint8_t *gscratch, int32_t *etgt, int32_t *esrc, uint32_t *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -319,7 +399,8 @@ prune_insert_kernel(DevIndex ix, int32_t *graph, int64_t pos0, int64_t nb, int n
       const int64_t it = bi * nT + ti;
       const int m = min(vis_n[it], vcap);
       for (int i = lane; i < m; i += 32) {
-        S.skey[nc + i] = make_key(0u, vis_d[it * vcap + i]);
+        // Weight-JAG lists hold D_A^w, not dist: sort by id only, recompute dist below
+        S.skey[nc + i] = weighted ? (uint64_t)vis_ids[it * vcap + i] : make_key(0u, vis_d[it * vcap + i]);
         S.sid[nc + i] = vis_ids[it * vcap + i];
       }
       nc += m;
@@ -350,8 +431,18 @@ prune_insert_kernel(DevIndex ix, int32_t *graph, int64_t pos0, int64_t nb, int n
       w += __popc(m);
     }
     __syncwarp();
+    if (weighted) {
+      QChunks<CPL, JAG_VEC_F32> xp;
+      load_point<P, CPL>(ix.x + p * ix.xs, (int)ix.xs, xp);
+      for (int b = 0; b < w; b += 32) {
+        const int m = min(32, w - b);
+        const float dv = candidate_distances<P, CPL>(ix, xp, S.cid + b, m);
+        if (lane < m) S.cdist[b + lane] = dv;
+      }
+      __syncwarp();
+    }
     int32_t *row = graph + p * ix.R;
-    joint_prune<P, CPL>(ix, p, S, w, cmax, thr + p * nT, nT, alpha2, row);
+    joint_prune<P, CPL>(ix, p, S, w, cmax, thr + p * nT, nT, alpha2, weighted, row);
     for (int r = lane; r < ix.R; r += 32) {
       const int32_t v = row[r];
       etgt[bi * ix.R + r] = v;
@@ -399,8 +490,8 @@ __global__ void edge_scatter_kernel(const int32_t *etgt, const int32_t *esrc, in
 
 template <int P, int CPL>
 __global__ void __launch_bounds__(kPruneWarps * 32)
-edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, const uint32_t *thr, float alpha2,
-                  int cmax_s, int cmax_g, uint8_t *gscratch, EdgeState E, uint32_t *status) {
+edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, const uint32_t *thr, int weighted,
+                  float alpha2, int cmax_s, int cmax_g, uint8_t *gscratch, EdgeState E, uint32_t *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const PruneSmem Ss = carve_prune(smem + warp * prune_smem_bytes(cmax_s), cmax_s);
@@ -439,7 +530,7 @@ edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, cons
         if (lane < m) S.cdist[b + lane] = dv;
       }
       __syncwarp();
-      joint_prune<P, CPL>(ix, v, S, nc, cmax, thr + (int64_t)v * nT, nT, alpha2, row);
+      joint_prune<P, CPL>(ix, v, S, nc, cmax, thr + (int64_t)v * nT, nT, alpha2, weighted, row);
     }
     __syncwarp();
     if (lane == 0) { E.tcount[v] = 0; E.tfill[v] = 0; }
@@ -495,8 +586,8 @@ static cudaError_t launch_build_search(const BuildLaunch &B, int64_t pos0, int64
   if (bps <= 0) return cudaErrorInvalidConfiguration;
   const int64_t items = nb * B.nT;
   const int64_t grid = std::min<int64_t>((int64_t)bps * dev_sms(), (items + kSearchWarps - 1) / kSearchWarps);
-  kern<<<(unsigned)grid, kSearchWarps * 32, smem, B.stream>>>(B.ix, pos0, nb, B.nT, B.thr, B.lb, hbits, s.vis_ids,
-                                                             s.vis_d, s.vis_n, vcap, s.work, s.status);
+  kern<<<(unsigned)grid, kSearchWarps * 32, smem, B.stream>>>(B.ix, pos0, nb, B.nT, B.thr, B.weighted, B.lb, hbits,
+                                                             s.vis_ids, s.vis_d, s.vis_n, vcap, s.work, s.status);
   return cudaGetLastError();
 }
 
@@ -508,7 +599,7 @@ static cudaError_t launch_prunes(const BuildLaunch &B, int64_t pos0, int64_t nb,
   cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t pgrid = std::min<int64_t>((nb + kPruneWarps - 1) / kPruneWarps, s.prune_blocks);
   pk<<<(unsigned)std::max<int64_t>(pgrid, 1), kPruneWarps * 32, smem, B.stream>>>(
-      B.ix, B.graph, pos0, nb, B.nT, B.thr, B.alpha2, s.vis_ids, s.vis_d, s.vis_n, vcap, cmax_s, cmax_g,
+      B.ix, B.graph, pos0, nb, B.nT, B.thr, B.weighted, B.alpha2, s.vis_ids, s.vis_d, s.vis_n, vcap, cmax_s, cmax_g,
       s.gscratch, s.etgt, s.esrc, s.status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -521,8 +612,27 @@ static cudaError_t launch_prunes(const BuildLaunch &B, int64_t pos0, int64_t nb,
   cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t agrid = std::min<int64_t>((ne + kPruneWarps - 1) / kPruneWarps, s.prune_blocks);
   ak<<<(unsigned)std::max<int64_t>(agrid, 1), kPruneWarps * 32, smem, B.stream>>>(
-      B.ix, B.graph, ne, B.nT, B.thr, B.alpha2, cmax_s, cmax_g, s.gscratch, s.E, s.status);
+      B.ix, B.graph, ne, B.nT, B.thr, B.weighted, B.alpha2, cmax_s, cmax_g, s.gscratch, s.E, s.status);
   return cudaGetLastError();
+}
+
+static cudaError_t launch_weights(const BuildLaunch &B, const Mult &mult, int64_t blocks) {
+  int P, CPL;
+  if (!row_mapping(B.ix.nchunks, &P, &CPL)) return cudaErrorInvalidValue;
+#define JAG_WCASE(PP, CC)                                                                                      \
+  if (P == PP && CPL == CC) {                                                                                  \
+    weights_kernel<PP, CC><<<(unsigned)blocks, kWgtWarps * 32, 0, B.stream>>>(B.ix, B.sample, B.seed, B.nT,   \
+                                                                             mult, B.thr);                     \
+    return cudaGetLastError();                                                                                 \
+  }
+  JAG_WCASE(8, 1)
+  JAG_WCASE(16, 1)
+  JAG_WCASE(32, 1)
+  JAG_WCASE(32, 2)
+  JAG_WCASE(32, 4)
+  JAG_WCASE(32, 8)
+#undef JAG_WCASE
+  return cudaErrorInvalidValue;
 }
 
 template <int CAP>
@@ -588,7 +698,14 @@ int run_build(BuildLaunch &B, int32_t *entry_out, char *msg, size_t msg_len) {
     Pct pct;
     for (int i = 0; i < 4; ++i) pct.v[i] = B.pct[i];
     const int64_t blocks = std::min<int64_t>((n + kThrWarps - 1) / kThrWarps, (int64_t)dev_sms() * 8);
-    thresholds_kernel<<<(unsigned)blocks, kThrWarps * 32, 0, B.stream>>>(B.ix, B.sample, B.seed, B.nT, pct, B.thr);
+    if (B.weighted) {
+      Mult mult;
+      for (int i = 0; i < 8; ++i) mult.v[i] = B.mult[i];
+      const int64_t wb = std::min<int64_t>((n + kWgtWarps - 1) / kWgtWarps, (int64_t)dev_sms() * 16);
+      JAG_TRY(launch_weights(B, mult, wb));
+    } else {
+      thresholds_kernel<<<(unsigned)blocks, kThrWarps * 32, 0, B.stream>>>(B.ix, B.sample, B.seed, B.nT, pct, B.thr);
+    }
     JAG_TRY(cudaGetLastError());
     centroid_kernel<<<(B.ix.d + 127) / 128, 128, 0, B.stream>>>(B.ix, s.centroid);
     JAG_TRY(cudaMemsetAsync(s.best, 0xFF, 16, B.stream));

@@ -91,6 +91,8 @@ struct BuildLaunch {
   uint64_t seed;
   int32_t lb;
   float alpha2;
+  int32_t weighted;         // Weight-JAG: thr holds fp32 weights mult[i] * h_p
+  double mult[8];
   cudaStream_t stream;
 };
 // Returns 0 on success, else a jag_status code; msg receives a description.

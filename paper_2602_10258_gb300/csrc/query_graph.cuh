@@ -14,6 +14,10 @@ namespace jag {
 // D_F (Algorithm 2) for the graph-routed ones.  With fp32 rows it writes the
 // answers; with BF16 / FP8 rows it leaves the ids of the leading rr passing
 // entries of the final list for the fp32 re-rank.
+// Lanes per row of the graph search for rows of 17..32 chunks (a 128-d fp32
+// row is 32 chunks).
+constexpr int kGraphLanes = 32;
+
 template <int CAP, int P, int CPL, int FMT, bool POL>
 __global__ void __launch_bounds__(kSearchWarps * 32, CPL == 1 ? 8 : 1)
 query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
@@ -94,6 +98,7 @@ static cudaError_t launch_graph_cap(const SearchLaunch &L, int P, int CPL) {
   JAG_GCASE(16, 1)
   JAG_GCASE(32, 1)
   JAG_GCASE(32, 2)
+  JAG_GCASE(kGraphLanes, 32 / kGraphLanes)
   if constexpr (!POL) {
     JAG_GCASE(32, 4)
     if constexpr (FMT == JAG_VEC_F32) {
@@ -109,6 +114,9 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L) {
   int P, CPL;
   const int nch = FMT == JAG_VEC_F32 ? L.ix.nchunks : L.ix.qchunks;
   if (!row_mapping(nch, &P, &CPL)) return cudaErrorInvalidValue;
+  // rows of 17..32 chunks: kGraphLanes lanes per row, the first butterfly
+  // levels folded into registers (fewer shuffles per row, more rows per load)
+  if (nch > 16 && nch <= 32) { P = kGraphLanes; CPL = 32 / kGraphLanes; }
   if (L.has_policy) {
     if (list_capacity(L.ls) <= 128) return launch_graph_cap<128, FMT, true>(L, P, CPL);
     return launch_graph_cap<256, FMT, true>(L, P, CPL);

@@ -171,11 +171,21 @@ struct QChunks {
 // Distances from the search point (lane-held chunks q) to the nc rows whose
 // ids are cid[0..nc), rows stored in format FMT; lane c < nc returns the
 // distance of candidate c.
+//
+// Lane mapping: a row is held by a group of P lanes; lane lig holds chunks
+// lig + j*P (j < CPL).  Chunk g belongs to canonical accumulator g mod 32, so
+// a lane with P < 32 keeps F = 32/P of the canonical accumulators (chunk j in
+// accumulator j mod F, in chunk order) and performs the butterfly levels
+// 16..P in registers before the shuffle levels P/2..1: the same additions in
+// the same order as the 32-lane canonical reduction (levels that would add
+// exact zeros are skipped).
 template <int P, int CPL, int ROWS = 4, int FMT = JAG_VEC_F32>
 __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const QChunks<CPL, FMT> &q,
                                                      const uint32_t *cid, int nc) {
   constexpr int VPW = 32 / P;                        // rows per warp-wide load
   constexpr int U = VPW >= ROWS ? 1 : ROWS / VPW;    // loads in flight per lane (ROWS rows per warp)
+  constexpr int F = 32 / P;                          // canonical accumulators per lane
+  constexpr int NA = CPL < F ? CPL : F;              // of which can be non-zero
   const int lane = threadIdx.x & 31;
   const int grp = lane / P, lig = lane % P;
   const int nch = FMT == JAG_VEC_F32 ? ix.nchunks : ix.qchunks;
@@ -195,7 +205,7 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const Q
         if (FMT == JAG_VEC_FP8) sc[s] = ok ? __ldg(ix.qscale + id) : 1.f;
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
-          const int ch = lig + j * 32;
+          const int ch = lig + j * P;
           xv[s][j] = (ok && ch < nch) ? ld_chunk_u4(row + ch * 16) : make_uint4(0, 0, 0, 0);
         }
       }
@@ -205,8 +215,18 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const Q
     for (int s = 0; s < U; ++s) {
       acc[s] = 0.f;
       if (base + s * VPW < nc) {   // warp-uniform
+        float a[NA];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) acc[s] = chunk_acc<FMT>(acc[s], q.v[j], xv[s][j], sc[s]);
+        for (int i = 0; i < NA; ++i) a[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) a[j % F] = chunk_acc<FMT>(a[j % F], q.v[j], xv[s][j], sc[s]);
+#pragma unroll
+        for (int h = F / 2; h >= 1; h >>= 1) {
+#pragma unroll
+          for (int i = 0; i < h; ++i)
+            if (i + h < NA) a[i] = __fadd_rn(a[i], a[i + h]);
+        }
+        acc[s] = a[0];
       }
     }
     group_reduce_n<P, U>(acc);
@@ -221,14 +241,15 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const Q
 }
 
 // Lane chunks of a search point given as a contiguous fp32 row of d values
-// (not necessarily 16-byte aligned); elements past d are zero.
+// (not necessarily 16-byte aligned); elements past d are zero.  Lane lig of a
+// P-lane group holds chunks lig + j*P (the mapping of candidate_distances).
 template <int P, int CPL, int FMT = JAG_VEC_F32>
 __device__ __forceinline__ void load_point(const float *row, int d, QChunks<CPL, FMT> &q) {
   constexpr int E = RowFmt<FMT>::E;
   const int lig = (threadIdx.x & 31) % P;
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    const int e0 = (lig + j * 32) * E;
+    const int e0 = (lig + j * P) * E;
 #pragma unroll
     for (int i = 0; i < RowFmt<FMT>::Q4; ++i) {
       const int e = e0 + 4 * i;
@@ -242,8 +263,14 @@ __device__ __forceinline__ void load_point(const float *row, int d, QChunks<CPL,
 
 // First-key policies.  A policy with kEdgeAttr reads the neighbour's
 // attribute from the edge table in the same wave as the neighbour id.
+// A key policy gives, for candidate u, a 32-bit word (operator()), and the
+// 64-bit list key from that word and u's vector distance (key()).  With
+// kScalar the key is one number (no first component), so a full list cannot
+// reject a candidate before its distance is known.
 struct QueryKey {   // dist_F of the query's filter (Sec. 3.1)
   static constexpr bool kEdgeAttr = true;
+  static constexpr bool kScalar = false;
+  __device__ __forceinline__ uint64_t key(uint32_t w, float dist) const { return make_key(w, dist); }
   int32_t kind;
   uint64_t payload;
   const uint8_t *lut;
@@ -260,10 +287,31 @@ struct QueryKey {   // dist_F of the query's filter (Sec. 3.1)
 
 struct BuildKey {   // capped dist_A from base point p with threshold t (Sec. 3.2)
   static constexpr bool kEdgeAttr = false;   // the graph changes while it is built
+  static constexpr bool kScalar = false;
+  __device__ __forceinline__ uint64_t key(uint32_t w, float dist) const { return make_key(w, dist); }
   int64_t p;
   uint32_t t;
   __device__ __forceinline__ uint32_t operator()(const DevIndex &ix, int64_t u) const {
     return capped_distance(ix.dist_a, attribute_distance(ix, p, u), t);
+  }
+  __device__ __forceinline__ uint64_t edge_word(const DevIndex &, int64_t) const { return 0; }
+  __device__ __forceinline__ uint32_t from_word(uint64_t) const { return 0; }
+};
+
+// Weight-JAG's build comparator D_A^w(p, u) = w dist_A(a_p, a_u) + dist(x_p,
+// x_u) (the weighted variant of Sec. 3), one fp32 fma; the word carries
+// dist_A as an fp32 value.
+struct WeightKey {
+  static constexpr bool kEdgeAttr = false;
+  static constexpr bool kScalar = true;
+  int64_t p;
+  float w;
+  __device__ __forceinline__ uint32_t operator()(const DevIndex &ix, int64_t u) const {
+    const uint32_t da = attribute_distance(ix, p, u);
+    return f2u(ix.dist_a == JAG_F_RANGE_F32 ? u2f(da) : __uint2float_rn(da));
+  }
+  __device__ __forceinline__ uint64_t key(uint32_t w_bits, float dist) const {
+    return make_key(0u, __fmaf_rn(w, u2f(w_bits), dist));
   }
   __device__ __forceinline__ uint64_t edge_word(const DevIndex &, int64_t) const { return 0; }
   __device__ __forceinline__ uint32_t from_word(uint64_t) const { return 0; }
@@ -437,7 +485,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
     const float d0 = candidate_distances<P, CPL, 4, FMT>(ix, q, S.cid, 1);
     const uint32_t k0 = key1(ix, s);
     const float d0b = __shfl_sync(kFull, d0, 0);
-    if (lane == 0) { S.bkey[0] = make_key(k0, d0b); S.bid[0] = (uint32_t)s; }
+    if (lane == 0) { S.bkey[0] = key1.key(k0, d0b); S.bid[0] = (uint32_t)s; }
   }
   __syncwarp();
   int cnt = 1, start = 0;
@@ -469,7 +517,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       bool cand = u >= 0;
       if (cand) {
         k1 = KeyFn::kEdgeAttr ? key1.from_word(aw) : key1(ix, u);
-        cand = !(full && k1 > (uint32_t)(tkey >> 32));
+        cand = KeyFn::kScalar || !(full && k1 > (uint32_t)(tkey >> 32));
       }
       bool inserted = false, keep = false;
       if (cand) keep = visit_insert(S.hash, hbits, (uint32_t)u, inserted);
@@ -489,7 +537,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       uint64_t ck = kNoKey;
       uint32_t cv = kEmptySlot;
       if (lane < nc) {
-        ck = make_key(S.ck1[lane], dist);
+        ck = key1.key(S.ck1[lane], dist);
         cv = S.cid[lane];
         if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
       }

@@ -39,7 +39,8 @@ class BuildParams(C.Structure):
                 ("R", C.c_int32), ("l_b", C.c_int32), ("alpha", C.c_float),
                 ("n_thresholds", C.c_int32), ("threshold_pct", C.c_int32 * 4),
                 ("sample_size", C.c_int32), ("seed", C.c_uint64), ("storage", C.c_int32),
-                ("device", C.c_int32), ("graph", C.c_void_p), ("entry", C.c_int64)]
+                ("device", C.c_int32), ("graph", C.c_void_p), ("entry", C.c_int64),
+                ("n_weights", C.c_int32), ("reserved", C.c_int32), ("weight_mult", C.c_double * 8)]
 
 
 class SearchArgs(C.Structure):
@@ -76,7 +77,8 @@ class ServeTiming(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("R", C.c_int32), ("storage", C.c_int32),
                 ("entry", C.c_int64), ("device_bytes", C.c_int64), ("build_seconds", C.c_double),
-                ("n_thresholds", C.c_int32), ("dist_a", C.c_int32)]
+                ("n_thresholds", C.c_int32), ("dist_a", C.c_int32), ("weighted", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_search_noalloc", "jag_get_info",
@@ -161,8 +163,9 @@ def _np_ptr(a):
 
 def jag_build(x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=JAG_F_RANGE_I32, R=32,
               l_b=64, alpha=1.2, thresholds=(100, 1, 0), sample_size=500, seed=0,
-              storage=JAG_VEC_F32, device=0, graph=None, entry=0):
-    """Build (or upload) an index from host arrays; returns an opaque handle."""
+              storage=JAG_VEC_F32, device=0, graph=None, entry=0, weights=None):
+    """Build (or upload) an index from host arrays; returns an opaque handle.
+    weights: multipliers of h for a Weight-JAG build (None: Threshold-JAG)."""
     L = load()
     x = np.ascontiguousarray(x, np.float32)
     keep = [x]
@@ -188,6 +191,10 @@ def jag_build(x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=JAG_F_RANG
     p.sample_size, p.seed, p.storage, p.device = int(sample_size), int(seed), int(storage), int(device)
     p.graph = _np_ptr(g)
     p.entry = int(entry)
+    if weights is not None:
+        p.n_weights = len(weights)
+        for i, c in enumerate(weights):
+            p.weight_mult[i] = float(c)
     h = C.c_void_p()
     _check(L.jag_build(C.byref(p), C.byref(h)))
     return h
@@ -322,9 +329,9 @@ class Index:
 
     def __init__(self, x, attr_i32=None, attr_f32=None, attr_mask=None, dist_a=JAG_F_RANGE_I32, R=32,
                  l_b=64, alpha=1.2, thresholds=(100, 1, 0), sample_size=500, seed=0,
-                 storage=JAG_VEC_F32, device=0, graph=None, entry=0):
+                 storage=JAG_VEC_F32, device=0, graph=None, entry=0, weights=None):
         self.h = jag_build(x, attr_i32, attr_f32, attr_mask, dist_a, R, l_b, alpha, thresholds,
-                           sample_size, seed, storage, device, graph, entry)
+                           sample_size, seed, storage, device, graph, entry, weights)
         self.d = int(np.asarray(x).shape[1])
 
     @classmethod
