@@ -42,6 +42,7 @@ LB = 64
 THRESHOLDS = (100, 0)
 ALPHA = 1.2
 S0 = 10000
+SCAN_CAP = 8192
 
 
 def workload_desc(n, d, nq):
@@ -224,7 +225,7 @@ def run_ours(args):
     chosen = None
     band_min_beam = {}
     for beam in BEAMS:
-        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0)
+        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
         torch.cuda.synchronize()
         rec = recall_at_k(ids.cpu().numpy(), gt_ids, gt_d)
         per = {}
@@ -244,7 +245,7 @@ def run_ours(args):
         chosen = BEAMS[-1]
 
     # counters pass: algorithmic bytes of one launch (untimed)
-    jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, cnt, stream, s0=S0)
+    jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, cnt, stream, s0=S0, scan_cap=SCAN_CAP)
     torch.cuda.synchronize()
     c = cnt.cpu().numpy().astype(np.int64)
     graph_q = c[:, 3] == 0
@@ -265,7 +266,7 @@ def run_ours(args):
         ke.record(stream)
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0)
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -275,7 +276,7 @@ def run_ours(args):
             flush.fill_(float(i))
             s_ev, e_ev, kb, ke = ev[i]
             s_ev.record(stream)
-            jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, ev_begin=kb, ev_end=ke)
+            jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP, ev_begin=kb, ev_end=ke)
             e_ev.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -301,7 +302,7 @@ def run_ours(args):
             flush.fill_(2.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            jag.jag_search(idx.h, qb, fb, at, K, beam_b, ib, db, None, stream, s0=S0)
+            jag.jag_search(idx.h, qb, fb, at, K, beam_b, ib, db, None, stream, s0=S0, scan_cap=SCAN_CAP)
             b.record(stream)
             torch.cuda.synchronize()
             if r:
@@ -318,13 +319,13 @@ def run_ours(args):
     pin_ids = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     pin_d = torch.empty((nq, K), dtype=torch.float32).pin_memory()
     for _ in range(2):
-        jag.jag_search_host(idx.h, pin_q, pin_f, None, K, chosen, s0=S0, out_ids=pin_ids, out_dist=pin_d)
+        jag.jag_search_host(idx.h, pin_q, pin_f, None, K, chosen, s0=S0, scan_cap=SCAN_CAP, out_ids=pin_ids, out_dist=pin_d)
     e2e_t = []
     for _ in range(max(3, min(args.steps, 10))):
         flush.fill_(3.0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        jag.jag_search_host(idx.h, pin_q, pin_f, None, K, chosen, s0=S0, out_ids=pin_ids, out_dist=pin_d)
+        jag.jag_search_host(idx.h, pin_q, pin_f, None, K, chosen, s0=S0, scan_cap=SCAN_CAP, out_ids=pin_ids, out_dist=pin_d)
         e2e_t.append(time.perf_counter() - t1)
     e2e_rec = recall_at_k(pin_ids.numpy(), gt_ids, gt_d)
     assert np.array_equal(pin_ids.numpy(), ids.cpu().numpy())
@@ -386,7 +387,7 @@ def run_ours(args):
         "config": {"workload": workload_desc(w.n, w.d, nq), "beam": chosen, "k": K, "R": R,
                    "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.1f" % (LB, list(THRESHOLDS), ALPHA),
                    "build_seconds": round(build_s, 2), "index_device_bytes": info["device_bytes"],
-                   "scan_threshold_s0": S0, "l2": "inputs larger than L2 and L2 flushed between steps",
+                   "scan_threshold_s0": S0, "scan_cap": SCAN_CAP, "l2": "inputs larger than L2 and L2 flushed between steps",
                    "recall_at_beam": recall_chosen, "bands": bands_out,
                    "beam_sweep": {str(b): v for b, v in sweep.items()},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -417,7 +418,7 @@ def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stre
     dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
     chosen, per = None, None
     for beam in BEAMS:
-        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0)
+        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
         torch.cuda.synchronize()
         rec = recall_at_k(ids.cpu().numpy(), gt_ids, gt_d)
         per = {}
@@ -431,7 +432,7 @@ def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stre
     if chosen is None:
         chosen = BEAMS[-1]
     for _ in range(3):
-        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0)
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
     ts, ks = [], []
     for i in range(steps):
         flush.fill_(float(i))
@@ -440,7 +441,7 @@ def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stre
         ka.record(stream)
         kb.record(stream)
         a.record(stream)
-        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, ev_begin=ka, ev_end=kb)
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP, ev_begin=ka, ev_end=kb)
         b.record(stream)
         ts.append((a, b, ka, kb))
     torch.cuda.synchronize()
@@ -488,7 +489,7 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
         trace = tr.run(X, y, t, epochs=60, batch=512, lr=2e-3, lam=1.0)
         for scale in (64.0, 80.0, 96.0, 112.0, 128.0):
             lp = jag.Policy.learned(params, h0=32, tau=0.0, stop_scale=scale)
-            jag.jag_search(fidx.h, q, ft, at, K, base, ids, dd, cnt, stream, s0=S0, policy=lp)
+            jag.jag_search(fidx.h, q, ft, at, K, base, ids, dd, cnt, stream, s0=S0, scan_cap=SCAN_CAP, policy=lp)
             torch.cuda.synchronize()
             rec = recall_at_k(ids.cpu().numpy(), gt_ids, gt_d)
             per = {name: float(np.mean(rec[(band == j) & ~np.isnan(rec)])) for j, (_, _, name) in enumerate(BANDS)
@@ -501,13 +502,13 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
 
     def timed(beam, pol):
         for _ in range(3):
-            jag.jag_search(fidx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, policy=pol)
+            jag.jag_search(fidx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP, policy=pol)
         evs = []
         for i in range(steps):
             flush.fill_(float(i))
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            jag.jag_search(fidx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, policy=pol)
+            jag.jag_search(fidx.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP, policy=pol)
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize()
@@ -541,7 +542,7 @@ def measure_serving(jag, idx, w, beam, band, gt_ids, gt_d, sat_qps, n_req=2000, 
         first = np.array([rng.integers(0, len(w.q) - s + 1) for s in sizes], np.int64)
         rate = load * sat_qps / float(sizes.mean())            # requests per second
         arrival = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        srv = jag.Server(idx, K, beam, s0=S0, max_queries=1 << 17)
+        srv = jag.Server(idx, K, beam, s0=S0, scan_cap=SCAN_CAP, max_queries=1 << 17)
         t1 = time.perf_counter()
         ids, dist, lat, devs = srv.replay(arrival, sizes, first, w.q, w.filters, w.aux, timeout_s=300.0)
         wall = time.perf_counter() - t1
@@ -599,7 +600,7 @@ def cpu_baseline(w, idx, beam, gt_ids, gt_d, budget_s=15.0):
     while done < len(w.q) and t_total < budget_s:
         sl = slice(done, min(done + 200, len(w.q)))
         t1 = time.perf_counter()
-        ids, _, cn = O.query(ox, w.q[sl], w.filters[sl], w.aux, K, beam, s0=S0, scan_cap=8192, nthreads=cores)
+        ids, _, cn = O.query(ox, w.q[sl], w.filters[sl], w.aux, K, beam, s0=S0, scan_cap=SCAN_CAP, nthreads=cores)
         t_total += time.perf_counter() - t1
         ids_all.append(ids)
         cnt_all.append(cn)
@@ -634,7 +635,7 @@ def run_reference(args):
         s = (i * per) % len(w.q)
         sl = slice(s, min(s + per, len(w.q)))
         t1 = time.perf_counter()
-        O.query(ox, w.q[sl], w.filters[sl], w.aux, K, beam, s0=S0, scan_cap=8192, nthreads=cores)
+        O.query(ox, w.q[sl], w.filters[sl], w.aux, K, beam, s0=S0, scan_cap=SCAN_CAP, nthreads=cores)
         dt = time.perf_counter() - t1
         if i >= args.warmup:
             times.append((sl.stop - sl.start, dt))
@@ -666,13 +667,14 @@ def run_profile(args):
     ids = torch.empty((len(w.q), K), dtype=torch.int32, device=q.device)
     dd = torch.empty((len(w.q), K), dtype=torch.float32, device=q.device)
     for _ in range(args.steps):
-        jag.jag_search(idx.h, q, ft, None, K, args.beam, ids, dd, None, None, s0=S0)
+        jag.jag_search(idx.h, q, ft, None, K, args.beam, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
     torch.cuda.synchronize()
     log("profile run done: %d searches of %d queries at beam %d" % (args.steps, len(w.q), args.beam))
     idx.close()
 
 
 def main():
+    global S0, SCAN_CAP
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
@@ -690,7 +692,13 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=200)
     ap.add_argument("--profile", action="store_true", help="fixed-beam searches only (for ncu)")
     ap.add_argument("--beam", type=int, default=192)
+    ap.add_argument("--s0", type=int, default=None, help="scan route threshold (default %d)" % S0)
+    ap.add_argument("--scan-cap", type=int, default=None, help="largest scanned set (default %d)" % SCAN_CAP)
     args = ap.parse_args()
+    if args.s0 is not None:
+        S0 = args.s0
+    if args.scan_cap is not None:
+        SCAN_CAP = args.scan_cap
     if args.warmup < 3:
         args.warmup = 3
     if args.profile:

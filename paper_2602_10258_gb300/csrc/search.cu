@@ -247,7 +247,7 @@ scan_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
         if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
       }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
       __syncwarp();   // rows[cur] and cids[cur] are reused by round r + 2
     }
     uint64_t *pk = part_key + (qi * ntiles + t) * k;
@@ -306,7 +306,7 @@ merge_scan_kernel(const DevIndex ix, const jag_filter *filters, const QueryPlan 
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -361,7 +361,7 @@ brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fi
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
     int r0;
-    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+    cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
   }
   for (int j = lane; j < k; j += 32) {
     pk[j] = j < cnt ? S.bkey[j] : kNoKey;
@@ -390,7 +390,7 @@ merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const 
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -436,7 +436,7 @@ rerank_kernel(DevIndex ix, const float *queries, int d, const QueryPlan *plans, 
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
     int r0;
-    cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+    cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
 }

@@ -110,7 +110,12 @@ __device__ __forceinline__ int list_rank(const uint64_t *bkey, const uint32_t *b
 // Merge the lane-held candidates (any order; invalid = kNoKey, distinct ids)
 // into L[0..cnt): keep the best ls, drop candidates already in L.  Returns
 // the new count; r0 receives the smallest insertion position (cnt if none).
-template <int CAP>
+//
+// BSEARCH: an entry's shift is found by a 5-step search of the new keys'
+// sorted ranks (srank, 32 words of shared memory) -- cheaper for the long
+// lists of the graph search; otherwise by one shuffle per new key -- smaller
+// code, better for the k-entry lists of the exact scans.
+template <int CAP, bool BSEARCH = true>
 __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, int cnt, int ls, uint64_t ck,
                                                 uint32_t cv, int &r0, uint32_t *srank) {
   const int lane = threadIdx.x & 31;
@@ -133,11 +138,13 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
     crank += key_less(ok, oi, ck, cv) ? 1 : 0;
   }
   r0 = (int)__reduce_min_sync(kFull, valid ? (unsigned)rank : 0xFFFFFFFFu);
-  // the new keys' ranks in L, in the new keys' order (non-decreasing), padded
-  const int nv = __popc(vm);
-  if (valid) srank[crank] = (uint32_t)rank;
-  if (lane >= nv) srank[lane] = 0xFFFFFFFFu;
-  __syncwarp();
+  if (BSEARCH) {
+    // the new keys' ranks in L, in the new keys' order (non-decreasing), padded
+    const int nv = __popc(vm);
+    if (valid) srank[crank] = (uint32_t)rank;
+    if (lane >= nv) srank[lane] = 0xFFFFFFFFu;
+    __syncwarp();
+  }
   // entry j moves right by the number of new keys ranked at or before j (a
   // 5-step search of srank); chunks from the back never overwrite an entry
   // not yet read
@@ -146,10 +153,15 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
     uint64_t ek = 0;
     uint32_t ei = 0;
     if (j < cnt) { ek = bkey[j]; ei = bid[j]; }
-    int sh = srank[31] <= (uint32_t)j ? 32 : 0;
-    if (sh == 0) {
+    int sh = 0;
+    if (BSEARCH) {
+      sh = srank[31] <= (uint32_t)j ? 32 : 0;
+      if (sh == 0) {
 #pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) sh += (srank[sh + step - 1] <= (uint32_t)j) ? step : 0;
+        for (int step = 16; step >= 1; step >>= 1) sh += (srank[sh + step - 1] <= (uint32_t)j) ? step : 0;
+      }
+    } else {
+      for (uint32_t m = vm; m; m &= m - 1) sh += (__shfl_sync(kFull, rank, __ffs(m) - 1) <= j) ? 1 : 0;
     }
     __syncwarp();
     if (j < cnt && j + sh < ls) { bkey[j + sh] = ek; bid[j + sh] = ei; }

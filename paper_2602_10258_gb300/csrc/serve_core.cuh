@@ -133,7 +133,7 @@ __device__ __forceinline__ int scan_merge(const DevIndex &ix, const QChunks<CPLF
     if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
   }
   int r0;
-  return merge_candidates<CAP>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+  return merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
 }
 
 // Exact top-k over the ids of a sorted-column slice (the scan route of
