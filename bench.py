@@ -400,7 +400,8 @@ def run_ours(args):
         "forms": forms,
         "serving": serving,
         "clocks": clk.summary(),
-        "gpu_launches": int(args.steps * 3),
+        # per step: prep, graph search, scan work items, scan tiles, scan merge
+        "gpu_launches": int(args.steps * 5),
     }
     if rank == 0:
         print(json.dumps(out))
