@@ -655,6 +655,93 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_serve_large(args):
+    """The serving form at its own scale: N = 10M, d = 100, BF16 rows (fp32
+    re-rank), float attribute U[0,1), range filters of width log-uniform in
+    [1e-4, 1].  Picks the smallest beam with recall@10 >= 0.95 in every band
+    on a ground-truth sample (else the largest beam, and says so), times the
+    batch search, then replays Poisson traffic at 0.5x and 0.8x of that
+    throughput through the serve loop.  Prints one JSON line."""
+    import torch
+    from paper_2602_10258_gb300 import datagen as D
+    from paper_2602_10258_gb300 import jag
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    w = D.make_range_f32(n=args.large_n, d=100, nq=10000, seed=args.seed)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    thr = tuple(int(v) for v in args.large_thresholds.split(","))
+    idx = jag.Index.from_workload(w, R=R, l_b=args.large_lb, alpha=ALPHA, thresholds=thr, storage=jag.JAG_VEC_BF16)
+    build_s = time.time() - t0
+    info = idx.info()
+    log("large: data %.1f s, build %.1f s (GPU %.1f s), %.2f GB on the device" % (
+        gen_s, build_s, info["build_seconds"], info["device_bytes"] / 1e9))
+    srt = np.sort(w.attr_f32)
+    fl = D.filter_fields(w.filters)
+    sel = (np.searchsorted(srt, fl["f_hi"], "right") - np.searchsorted(srt, fl["f_lo"], "left")) / w.n
+    band = band_of(sel)
+    nq = len(w.q)
+    q = torch.from_numpy(w.q).to(dev)
+    ft = jag.filters_to_device(w.filters, dev)
+    at = jag.aux_to_device(w.aux, dev)
+    ns = min(args.large_gt, nq)
+    t0 = time.time()
+    gt = torch.empty((ns, K), dtype=torch.int32, device=dev)
+    gd = torch.empty((ns, K), dtype=torch.float32, device=dev)
+    jag.jag_search(idx.h, q[:ns], ft, at, K, K, gt, gd, None, None, flags=jag.JAG_SEARCH_SCAN_ALL)
+    torch.cuda.synchronize()
+    gt, gd = gt.cpu().numpy(), gd.cpu().numpy()
+    gt_s = time.time() - t0
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    chosen, per_chosen, sweep, per = None, None, {}, {}
+    for beam in BEAMS:
+        jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy()[:ns], gt, gd)
+        per = {name: float(np.mean(rec[(band[:ns] == j) & ~np.isnan(rec)])) for j, (_, _, name) in enumerate(BANDS)
+               if ((band[:ns] == j) & ~np.isnan(rec)).any()}
+        sweep[beam] = {k: round(v, 4) for k, v in per.items()}
+        log("large beam %d: %s" % (beam, sweep[beam]))
+        if all(v >= 0.95 for v in per.values()):
+            chosen, per_chosen = beam, per
+            break
+    met = chosen is not None
+    if not met:
+        chosen, per_chosen = BEAMS[-1], per
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
+    evs = []
+    for i in range(min(args.steps, 20)):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    qps = nq / (ms / 1000.0)
+    gt_all = np.concatenate([gt, np.full((nq - ns, K), -1, np.int32)])
+    gd_all = np.concatenate([gd, np.full((nq - ns, K), np.inf, np.float32)])
+    serving = measure_serving(jag, idx, w, chosen, band, gt_all, gd_all, qps)
+    idx.close()
+    out = {"mode": "serve_large", "metric": METRIC, "unit": "queries/s", "dtype": "bf16 rows, f32 re-rank",
+           "data": "synthetic",
+           "config": {"workload": "float range, width log-uniform 1e-4..1, N=%d d=100 GMM-200, 10000 queries, "
+                                  "k=10, R=%d" % (w.n, R), "beam": chosen, "recall_0.95_met": met, "s0": S0,
+                      "scan_cap": SCAN_CAP,
+                      "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.1f" % (args.large_lb, list(thr), ALPHA),
+                      "build_seconds": round(build_s, 1), "gpu_build_seconds": round(info["build_seconds"], 1),
+                      "index_device_bytes": info["device_bytes"], "ground_truth_sample": ns,
+                      "ground_truth_seconds": round(gt_s, 1), "beam_sweep": {str(b): v for b, v in sweep.items()}},
+           "batch": {"qps": round(qps, 1), "ms_per_step": round(ms, 3), "recall": per_chosen},
+           "serving": serving}
+    print(json.dumps(out))
+
+
 def run_profile(args):
     """Build the index and run a few searches at a fixed beam (no sweep, no
     ground truth): the command profiled by ncu."""
@@ -692,6 +779,11 @@ def main():
     ap.add_argument("--ref-beam", type=int, default=192)
     ap.add_argument("--ref-queries", type=int, default=200)
     ap.add_argument("--profile", action="store_true", help="fixed-beam searches only (for ncu)")
+    ap.add_argument("--serve-large", action="store_true", help="the 10M BF16 serving form (not in the default run)")
+    ap.add_argument("--large-n", type=int, default=10_000_000)
+    ap.add_argument("--large-gt", type=int, default=2000, help="queries with ground truth in the large form")
+    ap.add_argument("--large-thresholds", default="100,10,0", help="threshold percentiles of the large form's build")
+    ap.add_argument("--large-lb", type=int, default=128, help="build beam of the large form")
     ap.add_argument("--beam", type=int, default=192)
     ap.add_argument("--s0", type=int, default=None, help="scan route threshold (default %d)" % S0)
     ap.add_argument("--scan-cap", type=int, default=None, help="largest scanned set (default %d)" % SCAN_CAP)
@@ -704,6 +796,8 @@ def main():
         args.warmup = 3
     if args.profile:
         run_profile(args)
+    elif args.serve_large:
+        run_serve_large(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

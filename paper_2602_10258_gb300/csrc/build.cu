@@ -472,6 +472,13 @@ __global__ void edge_count_kernel(const int32_t *etgt, int64_t ne, EdgeState E) 
   }
 }
 
+// Largest number of new back-edges of one target in the batch (ctr[3]).
+__global__ void edge_max_kernel(int64_t cap, EdgeState E) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap || (unsigned long long)i >= E.ctr[0]) return;
+  atomicMax(&E.ctr[3], (unsigned long long)E.tcount[E.tlist[i]]);
+}
+
 __global__ void edge_offset_kernel(int64_t cap, EdgeState E) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cap || (unsigned long long)i >= E.ctr[0]) return;
@@ -560,6 +567,8 @@ struct BuildScratch {
   unsigned long long *best = nullptr;
   uint8_t *gscratch = nullptr;   // per-warp candidate arrays of large prunes
   int64_t prune_blocks = 0;
+  uint8_t *big = nullptr;        // per-warp arrays for a batch whose hub targets need more
+  size_t big_bytes = 0;
   void *blocks[24] = {};
   int nblocks = 0;
 };
@@ -573,7 +582,13 @@ static cudaError_t balloc(BuildScratch &s, void **p, size_t bytes) {
 static void bfree(BuildScratch &s) {
   for (int i = 0; i < s.nblocks; ++i) cudaFree(s.blocks[i]);
   s.nblocks = 0;
+  if (s.big) cudaFree(s.big);
+  s.big = nullptr;
+  s.big_bytes = 0;
 }
+
+// Budget of the per-warp candidate arrays of oversized back-edge prunes.
+constexpr size_t kBigScratchBytes = size_t(1) << 30;
 
 template <int CAP, int P, int CPL>
 static cudaError_t launch_build_search(const BuildLaunch &B, int64_t pos0, int64_t nb, int hbits, BuildScratch &s,
@@ -606,13 +621,39 @@ static cudaError_t launch_prunes(const BuildLaunch &B, int64_t pos0, int64_t nb,
   const int64_t ne = nb * B.ix.R;
   const unsigned eb = (unsigned)((ne + 255) / 256);
   edge_count_kernel<<<eb, 256, 0, B.stream>>>(s.etgt, ne, s.E);
+  // A hub can receive more back-edges in one batch than the fixed per-warp
+  // arrays hold.  Size this batch's arrays from its largest target: fewer
+  // warps, each with room for a whole candidate set.
+  edge_max_kernel<<<eb, 256, 0, B.stream>>>(ne, s.E);
+  unsigned long long most = 0;
+  if ((e = cudaMemcpyAsync(&most, s.E.ctr + 3, sizeof(most), cudaMemcpyDeviceToHost, B.stream)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(B.stream)) != cudaSuccess) return e;
+  uint8_t *scratch = s.gscratch;
+  int cmax = cmax_g;
+  int64_t agrid = std::min<int64_t>((ne + kPruneWarps - 1) / kPruneWarps, s.prune_blocks);
+  if ((int64_t)most + B.ix.R > cmax_g) {
+    cmax = next_pow2((int)most + B.ix.R);
+    const size_t per = cand_bytes(cmax);
+    const int64_t warps = std::max<int64_t>(
+        kPruneWarps, std::min<int64_t>(s.prune_blocks * kPruneWarps, (int64_t)(kBigScratchBytes / per)));
+    agrid = std::max<int64_t>(1, std::min<int64_t>(agrid, warps / kPruneWarps));
+    const size_t need = per * (size_t)agrid * kPruneWarps;
+    if (s.big_bytes < need) {
+      if (s.big) cudaFree(s.big);
+      s.big = nullptr;
+      s.big_bytes = 0;
+      if ((e = cudaMalloc((void **)&s.big, need)) != cudaSuccess) return e;
+      s.big_bytes = need;
+    }
+    scratch = s.big;
+  }
   edge_offset_kernel<<<eb, 256, 0, B.stream>>>(ne, s.E);
   edge_scatter_kernel<<<eb, 256, 0, B.stream>>>(s.etgt, s.esrc, ne, s.E);
   auto ak = edge_apply_kernel<P, CPL>;
   cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int64_t agrid = std::min<int64_t>((ne + kPruneWarps - 1) / kPruneWarps, s.prune_blocks);
   ak<<<(unsigned)std::max<int64_t>(agrid, 1), kPruneWarps * 32, smem, B.stream>>>(
-      B.ix, B.graph, ne, B.nT, B.thr, B.weighted, B.alpha2, cmax_s, cmax_g, s.gscratch, s.E, s.status);
+      B.ix, B.graph, ne, B.nT, B.thr, B.weighted, B.alpha2, cmax_s, cmax, scratch, s.E, s.status);
   return cudaGetLastError();
 }
 
