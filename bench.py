@@ -167,12 +167,18 @@ def profile_traffic(src_hash):
     return float(t.group(1))
 
 
+# Sources the query path's kernels (graph search, scan, preparation) are
+# compiled from; a profile summary is valid while they are unchanged.
+QUERY_SOURCES = ["paper_2602_10258_gb300/csrc/" + f for f in (
+    "jag_internal.cuh", "launch.h", "launch_util.cuh", "plan.cuh", "query_graph.cuh", "search.cu",
+    "search_core.cuh", "search_f32.cu")] + ["include/jag.h"]
+
+
 def kernel_source_hash():
     import hashlib
     hs = hashlib.sha256()
-    cs = os.path.join(ROOT, "paper_2602_10258_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        hs.update(open(os.path.join(cs, f), "rb").read())
+    for f in QUERY_SOURCES:
+        hs.update(open(os.path.join(ROOT, f), "rb").read())
     return hs.hexdigest()[:16]
 
 
