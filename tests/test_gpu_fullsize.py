@@ -1,6 +1,8 @@
 """Parity at full size: the label workload the benchmark times (N=1,000,000,
-d=128, 10,000 queries, k=10, R=32) in the benchmark's launch configuration
-(one jag_search over the whole batch, default routing).
+d=128, 10,000 queries, k=10, R=32, thresholds {100%, 0%}) in the benchmark's
+launch configurations: one jag_search over the whole batch with s0 = 10,000
+at the beams the benchmark measures -- FP32 at 192, BF16 at 192, FP8 at 256,
+and BF16 with a beam / stop policy at base beam 256.
 
 The oracle cannot rebuild a 1M-point graph inside a test, so the graph here
 comes from the GPU build, whose output equals the oracle build bit for bit at
@@ -18,17 +20,17 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 jag = pytest.importorskip("paper_2602_10258_gb300.jag")
 
-N, NQ, K, BEAM = 1_000_000, 10_000, 10, 64
+N, NQ, K, BEAM, S0, CAP = 1_000_000, 10_000, 10, 192, 10_000, 8192
 
 
 @pytest.fixture(scope="module")
 def full():
     w = D.make_label_zipf(n=N, d=128, nq=NQ, seed=0)
-    gi = jag.Index.from_workload(w, R=32, l_b=64, alpha=1.2, thresholds=(100, 1, 0))
+    gi = jag.Index.from_workload(w, R=32, l_b=64, alpha=1.2, thresholds=(100, 0))
     info = gi.info()
     graph = gi.graph()
     q = torch.from_numpy(w.q).cuda()
-    ids, dist, cnt = gi.search(q, w.filters, w.aux, K, BEAM, counters=True)
+    ids, dist, cnt = gi.search(q, w.filters, w.aux, K, BEAM, counters=True, s0=S0, scan_cap=CAP)
     torch.cuda.synchronize()
     ox = O.Index.from_workload(w, R=32, graph=graph, entry=info["entry"])
     return w, gi, ox, graph, ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
@@ -50,7 +52,7 @@ def test_sampled_queries_match_oracle(full):
     w, gi, ox, graph, ids, dist, cnt = full
     rng = np.random.default_rng(123)
     sample = rng.choice(NQ, 48, replace=False)
-    rid, rd, rc = O.query(ox, w.q[sample], w.filters[sample], w.aux, K, BEAM, s0=2048, scan_cap=8192)
+    rid, rd, rc = O.query(ox, w.q[sample], w.filters[sample], w.aux, K, BEAM, s0=S0, scan_cap=CAP)
     assert (cnt[sample, 3] == rc[:, 3]).all()
     same = (ids[sample] == rid).all(axis=1)
     assert same.all(), "differs on %s" % sample[~same]
@@ -94,3 +96,52 @@ def test_recall_against_brute_force_sample(full):
     # only a floor that a broken search would miss, and exactness of the scan
     assert rec.mean() >= 0.7
     assert (rec[cnt[sample, 3] == 1] == 1.0).all()
+
+
+@pytest.mark.parametrize("fmt,beam", [(1, 192), (2, 256)])
+def test_low_precision_forms_match_oracle(full, fmt, beam):
+    """BF16 / FP8 rows on the same graph, at the beams the benchmark times."""
+    w, gi, ox, graph, *_ = full
+    info = gi.info()
+    fi = jag.Index.from_workload(w, R=32, graph=graph, entry=info["entry"], storage=fmt)
+    q = torch.from_numpy(w.q).cuda()
+    ids, dist, cnt = fi.search(q, w.filters, w.aux, K, beam, counters=True, s0=S0, scan_cap=CAP)
+    torch.cuda.synchronize()
+    ids, dist, cnt = ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
+    fi.close()
+    qx = O.Index.from_workload(w, R=32, graph=graph, entry=info["entry"], storage=fmt)
+    sample = np.random.default_rng(11 + fmt).choice(NQ, 32, replace=False)
+    rid, rd, rc = O.query(qx, w.q[sample], w.filters[sample], w.aux, K, beam, s0=S0, scan_cap=CAP)
+    assert (cnt[sample, 3] == rc[:, 3]).all()
+    assert (ids[sample] == rid).all(), "differs on %s" % sample[~(ids[sample] == rid).all(1)]
+    assert np.array_equal(dist[sample].view(np.uint32), rd.view(np.uint32))
+
+
+def test_policy_form_matches_oracle(full):
+    """BF16 rows with a beam / stop network at the benchmark's policy settings
+    (base beam 256, decision after 32 hops, stop scale 128): decisions and
+    answers equal the oracle's on sampled queries."""
+    from oracle import jag_mlp as M
+    w, gi, ox, graph, *_ = full
+    info = gi.info()
+    nl = len(jag.LADDER)
+    theta = M.init_params(nl, seed=21)
+    theta[-1] = 2.0                       # stop output near 2 * 128 hops
+    theta = theta.astype(np.float32)
+    fi = jag.Index.from_workload(w, R=32, graph=graph, entry=info["entry"], storage=1)
+    dec = torch.zeros((NQ, 4), dtype=torch.int32, device="cuda")
+    pol = jag.Policy.learned(torch.from_numpy(theta).cuda(), h0=32, tau=0.0, stop_scale=128.0, decisions=dec)
+    q = torch.from_numpy(w.q).cuda()
+    ids, dist, _ = fi.search(q, w.filters, w.aux, K, 256, s0=S0, scan_cap=CAP, policy=pol)
+    torch.cuda.synchronize()
+    ids, dist, dec = ids.cpu().numpy(), dist.cpu().numpy(), dec.cpu().numpy()
+    fi.close()
+    qx = O.Index.from_workload(w, R=32, graph=graph, entry=info["entry"], storage=1)
+    sample = np.random.default_rng(17).choice(NQ, 32, replace=False)
+    opol = O.Policy(O.POL_LEARNED, h0=32, theta=theta, tau=0.0, stop_scale=128.0, nq=len(sample),
+                    want_decisions=True)
+    rid, rd, rc = O.query_policy(qx, w.q[sample], w.filters[sample], w.aux, K, 256, opol, s0=S0, scan_cap=CAP)
+    graph_q = rc[:, 3] == 0
+    assert (ids[sample] == rid).all() and np.array_equal(dist[sample].view(np.uint32), rd.view(np.uint32))
+    assert (dec[sample][graph_q] == opol.decisions[graph_q]).all()
+    assert (opol.decisions[graph_q, 1] > 0).any()        # stop hops were set
