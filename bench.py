@@ -678,7 +678,8 @@ def run_serve_large(args):
     gen_s = time.time() - t0
     t0 = time.time()
     thr = tuple(int(v) for v in args.large_thresholds.split(","))
-    idx = jag.Index.from_workload(w, R=R, l_b=args.large_lb, alpha=ALPHA, thresholds=thr, storage=jag.JAG_VEC_BF16)
+    idx = jag.Index.from_workload(w, R=R, l_b=args.large_lb, alpha=args.large_alpha, thresholds=thr,
+                                  storage=jag.JAG_VEC_BF16)
     build_s = time.time() - t0
     info = idx.info()
     log("large: data %.1f s, build %.1f s (GPU %.1f s), %.2f GB on the device" % (
@@ -739,7 +740,8 @@ def run_serve_large(args):
            "config": {"workload": "float range, width log-uniform 1e-4..1, N=%d d=100 GMM-200, 10000 queries, "
                                   "k=10, R=%d" % (w.n, R), "beam": chosen, "recall_0.95_met": met, "s0": S0,
                       "scan_cap": SCAN_CAP,
-                      "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.1f" % (args.large_lb, list(thr), ALPHA),
+                      "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.2f" % (args.large_lb, list(thr),
+                                                                               args.large_alpha),
                       "build_seconds": round(build_s, 1), "gpu_build_seconds": round(info["build_seconds"], 1),
                       "index_device_bytes": info["device_bytes"], "ground_truth_sample": ns,
                       "ground_truth_seconds": round(gt_s, 1), "beam_sweep": {str(b): v for b, v in sweep.items()}},
@@ -790,6 +792,7 @@ def main():
     ap.add_argument("--large-gt", type=int, default=2000, help="queries with ground truth in the large form")
     ap.add_argument("--large-thresholds", default="100,10,0", help="threshold percentiles of the large form's build")
     ap.add_argument("--large-lb", type=int, default=128, help="build beam of the large form")
+    ap.add_argument("--large-alpha", type=float, default=ALPHA, help="pruning alpha of the large form")
     ap.add_argument("--beam", type=int, default=192)
     ap.add_argument("--s0", type=int, default=None, help="scan route threshold (default %d)" % S0)
     ap.add_argument("--scan-cap", type=int, default=None, help="largest scanned set (default %d)" % SCAN_CAP)
