@@ -147,8 +147,31 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
   }
   // entry j moves right by the number of new keys ranked at or before j (a
   // 5-step search of srank); chunks from the back never overwrite an entry
-  // not yet read
-  for (int t = (cnt - r0 + 31) / 32 - 1; t >= 0; --t) {
+  // not yet read.  With the search, two chunks are read, searched and written
+  // per round: entries only move right, so a chunk's writes land at or past
+  // its own start, which the round has already read.
+  int t = (cnt - r0 + 31) / 32 - 1;
+  if (BSEARCH) {
+    for (; t >= 1; t -= 2) {
+      const int j1 = r0 + 32 * t + lane, j0 = j1 - 32;
+      uint64_t ek1 = 0, ek0 = 0;
+      uint32_t ei1 = 0, ei0 = 0;
+      if (j1 < cnt) { ek1 = bkey[j1]; ei1 = bid[j1]; }
+      ek0 = bkey[j0];
+      ei0 = bid[j0];
+      int sh1 = srank[31] <= (uint32_t)j1 ? 32 : 0, sh0 = srank[31] <= (uint32_t)j0 ? 32 : 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        if (sh1 < 32) sh1 += (srank[sh1 + step - 1] <= (uint32_t)j1) ? step : 0;
+        if (sh0 < 32) sh0 += (srank[sh0 + step - 1] <= (uint32_t)j0) ? step : 0;
+      }
+      __syncwarp();
+      if (j1 < cnt && j1 + sh1 < ls) { bkey[j1 + sh1] = ek1; bid[j1 + sh1] = ei1; }
+      if (j0 + sh0 < ls) { bkey[j0 + sh0] = ek0; bid[j0 + sh0] = ei0; }
+      __syncwarp();
+    }
+  }
+  for (; t >= 0; --t) {
     const int j = r0 + 32 * t + lane;
     uint64_t ek = 0;
     uint32_t ei = 0;
