@@ -494,7 +494,7 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
         params = torch.from_numpy(D.mlp_init_params(nl, 0)).to(dev)
         tr = jag.Trainer(nl, params)
         trace = tr.run(X, y, t, epochs=60, batch=512, lr=2e-3, lam=1.0)
-        for scale in (64.0, 80.0, 96.0, 112.0, 128.0):
+        for scale in (64.0, 80.0, 96.0, 112.0, 128.0, 160.0, 192.0, 256.0):
             lp = jag.Policy.learned(params, h0=32, tau=0.0, stop_scale=scale)
             jag.jag_search(fidx.h, q, ft, at, K, base, ids, dd, cnt, stream, s0=S0, scan_cap=SCAN_CAP, policy=lp)
             torch.cuda.synchronize()

@@ -26,10 +26,11 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(ls);
-  const size_t wbytes = warp_smem_bytes(lcap, hbits) + (POL ? 128 * sizeof(float) : 0);
+  const size_t wbytes = warp_smem_bytes(lcap, hbits);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, hbits);
-  float *hbuf = reinterpret_cast<float *>(wb + warp_smem_bytes(lcap, hbits));
+  // the policy network's scratch: the candidate arrays cid, ck1 (free between hops)
+  float *hbuf = reinterpret_cast<float *>(S.cid);
   const int64_t sample = ix.n < 4096 ? ix.n : 4096;
   for (;;) {
     unsigned long long qi = 0;
@@ -76,7 +77,7 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
 template <int CAP, int P, int CPL, int FMT, bool POL>
 static cudaError_t launch_graph_one(const SearchLaunch &L) {
   const int lcap = list_slots(L.ls);
-  const size_t smem = (size_t)kSearchWarps * (warp_smem_bytes(lcap, L.hbits) + (POL ? 128 * sizeof(float) : 0));
+  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(lcap, L.hbits);
   auto kern = query_kernel<CAP, P, CPL, FMT, POL>;
   const int bps = blocks_per_sm(kern, smem);
   if (bps == 0) return cudaErrorInvalidConfiguration;

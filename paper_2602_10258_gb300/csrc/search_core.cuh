@@ -390,7 +390,7 @@ struct PolicyOut {
 };
 
 // Features of the list L[0..cnt) after the decision hop and the policy's
-// beam / stop (every lane returns the same).  hbuf: 128 floats of the warp.
+// beam / stop (every lane returns the same).  hbuf: 64 floats of the warp.
 __device__ __noinline__ static PolicyOut policy_decide(const jag_policy &pol, const WarpSmem &S, float *hbuf, int cnt, int k,
                                    int64_t est, int32_t kind, int fixed, float *feat_out, const int32_t *forced_q) {
   const int lane = threadIdx.x & 31;
@@ -440,20 +440,25 @@ __device__ __noinline__ static PolicyOut policy_decide(const jag_policy &pol, co
     hbuf[n] = acc > 0.f ? acc : 0.f;
   }
   __syncwarp();
+  // the second layer is held in registers until every lane has read the
+  // first, then takes its place (64 floats of scratch in all)
+  float h2[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int n = lane + 32 * h;
     float acc = b2[n];
     for (int i = 0; i < JAG_MLP_HIDDEN; ++i) acc = __fmaf_rn(bf16_value(w2[n * JAG_MLP_HIDDEN + i]), hbuf[i], acc);
-    hbuf[JAG_MLP_HIDDEN + n] = acc > 0.f ? acc : 0.f;
+    h2[h] = acc > 0.f ? acc : 0.f;
   }
+  __syncwarp();
+  hbuf[lane] = h2[0];
+  hbuf[lane + 32] = h2[1];
   __syncwarp();
   const int nl = pol.n_ladder;
   float out = -INFINITY;
   if (lane <= nl) {
     float acc = b3[lane];
-    for (int i = 0; i < JAG_MLP_HIDDEN; ++i)
-      acc = __fmaf_rn(bf16_value(w3[lane * JAG_MLP_HIDDEN + i]), hbuf[JAG_MLP_HIDDEN + i], acc);
+    for (int i = 0; i < JAG_MLP_HIDDEN; ++i) acc = __fmaf_rn(bf16_value(w3[lane * JAG_MLP_HIDDEN + i]), hbuf[i], acc);
     out = acc;
   }
   __syncwarp();
@@ -492,7 +497,7 @@ struct PolicyCtx {
   int64_t est;
   int32_t kind;
   int32_t k;
-  float *hbuf;             // 128 floats of the warp
+  float *hbuf;             // 64 floats of the warp (its free candidate scratch)
   float *feat_out;         // [12] or nullptr
   int32_t *dec_out;        // [4] or nullptr
   const int32_t *forced_q; // [2] or nullptr

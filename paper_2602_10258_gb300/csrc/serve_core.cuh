@@ -283,10 +283,10 @@ serve_kernel(ServeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(a.ls);
-  const size_t wbytes = warp_smem_bytes(lcap, a.hbits) + (POL ? 128 * sizeof(float) : 0);
+  const size_t wbytes = warp_smem_bytes(lcap, a.hbits);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, a.hbits);
-  float *hbuf = reinterpret_cast<float *>(wb + warp_smem_bytes(lcap, a.hbits));
+  float *hbuf = reinterpret_cast<float *>(S.cid);   // policy scratch: cid, ck1 (free between hops)
   for (;;) {
     long long c = 0;
     if (lane == 0) c = serve_claim(a);
