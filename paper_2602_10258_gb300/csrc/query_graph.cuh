@@ -18,19 +18,20 @@ namespace jag {
 // row is 32 chunks).
 constexpr int kGraphLanes = 32;
 
-template <int CAP, int P, int CPL, int FMT, bool POL>
+// POL: 0 plain, 1 with the search policy, 2 with the policy and its trace.
+template <int CAP, int P, int CPL, int FMT, int POL>
 __global__ void __launch_bounds__(kSearchWarps * 32, CPL == 1 ? 8 : 1)
 query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
              const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int rr, int32_t *rr_ids,
-             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work, jag_policy pol) {
+             int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work,
+             const __grid_constant__ jag_policy pol) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(ls);
-  const size_t wbytes = warp_smem_bytes(lcap, hbits);
+  const size_t wbytes = warp_smem_bytes(lcap, hbits) + (POL ? kPolicyCtxBytes : 0);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, hbits);
-  // the policy network's scratch: the candidate arrays cid, ck1 (free between hops)
-  float *hbuf = reinterpret_cast<float *>(S.cid);
+  PolicyCtx *pcs = reinterpret_cast<PolicyCtx *>(wb + warp_smem_bytes(lcap, hbits));
   const int64_t sample = ix.n < 4096 ? ix.n : 4096;
   for (;;) {
     unsigned long long qi = 0;
@@ -49,13 +50,16 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
     if constexpr (POL) {
       const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
                           : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
-      const PolicyCtx pc{&pol, est, f.kind, k, hbuf,
+      // the policy network's scratch: the candidate arrays cid, ck1 (free between hops)
+      if (lane == 0)
+        *pcs = PolicyCtx{&pol, est, f.kind, k, reinterpret_cast<float *>(S.cid),
                          pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr,
                          pol.decisions ? pol.decisions + (int64_t)qi * 4 : nullptr,
                          pol.forced ? pol.forced + (int64_t)qi * 2 : nullptr};
-      cnt = greedy_search<CAP, P, CPL, FMT, true>(ix, key, q, ls, hbits, S, sink, st, &pc);
+      __syncwarp();
+      cnt = greedy_search<CAP, P, CPL, FMT, POL>(ix, key, q, ls, hbits, S, sink, st, pcs);
     } else {
-      cnt = greedy_search<CAP, P, CPL, FMT, false>(ix, key, q, ls, hbits, S, sink, st);
+      cnt = greedy_search<CAP, P, CPL, FMT, 0>(ix, key, q, ls, hbits, S, sink, st);
     }
     if (FMT == JAG_VEC_F32) {
       write_answers(S, cnt, (int64_t)qi, k, out_ids, out_dist);
@@ -74,10 +78,10 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
   }
 }
 
-template <int CAP, int P, int CPL, int FMT, bool POL>
+template <int CAP, int P, int CPL, int FMT, int POL>
 static cudaError_t launch_graph_one(const SearchLaunch &L) {
   const int lcap = list_slots(L.ls);
-  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(lcap, L.hbits);
+  const size_t smem = (size_t)kSearchWarps * (warp_smem_bytes(lcap, L.hbits) + (POL ? kPolicyCtxBytes : 0));
   auto kern = query_kernel<CAP, P, CPL, FMT, POL>;
   const int bps = blocks_per_sm(kern, smem);
   if (bps == 0) return cudaErrorInvalidConfiguration;
@@ -91,7 +95,7 @@ static cudaError_t launch_graph_one(const SearchLaunch &L) {
   return cudaGetLastError();
 }
 
-template <int CAP, int FMT, bool POL>
+template <int CAP, int FMT, int POL>
 static cudaError_t launch_graph_cap(const SearchLaunch &L, int P, int CPL) {
 #define JAG_GCASE(PP, CC) \
   if (P == PP && CPL == CC) return launch_graph_one<CAP, PP, CC, FMT, POL>(L);
@@ -119,13 +123,15 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L) {
   // levels folded into registers (fewer shuffles per row, more rows per load)
   if (nch > 16 && nch <= 32) { P = kGraphLanes; CPL = 32 / kGraphLanes; }
   if (L.has_policy) {
-    if (list_capacity(L.ls) <= 128) return launch_graph_cap<128, FMT, true>(L, P, CPL);
-    return launch_graph_cap<256, FMT, true>(L, P, CPL);
+    // traces (decisions written) take the capacity-256 kernel for any beam
+    if (L.policy.decisions) return launch_graph_cap<256, FMT, 2>(L, P, CPL);
+    if (list_capacity(L.ls) <= 128) return launch_graph_cap<128, FMT, 1>(L, P, CPL);
+    return launch_graph_cap<256, FMT, 1>(L, P, CPL);
   }
   switch (list_capacity(L.ls)) {
-    case 64: return launch_graph_cap<64, FMT, false>(L, P, CPL);
-    case 128: return launch_graph_cap<128, FMT, false>(L, P, CPL);
-    case 256: return launch_graph_cap<256, FMT, false>(L, P, CPL);
+    case 64: return launch_graph_cap<64, FMT, 0>(L, P, CPL);
+    case 128: return launch_graph_cap<128, FMT, 0>(L, P, CPL);
+    case 256: return launch_graph_cap<256, FMT, 0>(L, P, CPL);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -491,7 +491,9 @@ __device__ __noinline__ static PolicyOut policy_decide(const jag_policy &pol, co
   return o;
 }
 
-// Per-search policy context passed to greedy_search.
+// Per-search policy context passed to greedy_search.  It lives in the
+// warp's shared memory (kPolicyCtxBytes after its search arrays), so that the
+// search loop keeps no register for it.
 struct PolicyCtx {
   const jag_policy *pol;   // nullptr: plain search
   int64_t est;
@@ -502,17 +504,25 @@ struct PolicyCtx {
   int32_t *dec_out;        // [4] or nullptr
   const int32_t *forced_q; // [2] or nullptr
 };
+constexpr size_t kPolicyCtxBytes = 64;
+static_assert(sizeof(PolicyCtx) <= kPolicyCtxBytes, "policy context slot");
 
 // Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
 // hold the final list L (count returned).
-template <int CAP, int P, int CPL, int FMT, bool POL = false, class KeyFn, class Sink>
+// POL: 0 plain search; 1 with the policy's decision at hop h0; 2 as 1, and the
+// trace of the search (decisions and the last hop that changed the first k
+// entries) written to pc->dec_out.
+template <int CAP, int P, int CPL, int FMT, int POL = 0, class KeyFn, class Sink>
 __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunks<CPL, FMT> &q, int ls,
                              int hbits, const WarpSmem &S, Sink &sink, SearchStats &st,
                              const PolicyCtx *pc = nullptr) {
-  const int ls0 = ls;
-  int stop = 0, learned = 0;
+  // policy state: the hop limit of the current phase -- the decision hop h0,
+  // then the stop hop (>= h0; a stop at h0 ends the search right after the
+  // decision, so a limit equal to h0 is always the decision's) -- and, for a
+  // trace, the last hop that changed the first k entries
+  int lim = (POL && pc->pol->mode != JAG_POLICY_PLAIN) ? pc->pol->h0 : 0x7FFFFFFF;
   int last_change = 0;
-  bool decided = false;
+  const int kq = POL == 2 ? pc->k : 0;
   const int lane = threadIdx.x & 31;
   const uint32_t hsize = 1u << hbits;
   for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
@@ -531,8 +541,22 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
   int cnt = 1, start = 0;
   st.hops = 0; st.seen = 0; st.dcs = 1;
   if (POL && pc->feat_out && lane < JAG_MLP_FEATURES) pc->feat_out[lane] = 0.f;
+  if (POL && pc->dec_out && lane == 0) {
+    pc->dec_out[0] = ls; pc->dec_out[1] = 0; pc->dec_out[2] = 0; pc->dec_out[3] = 0;
+  }
   for (;;) {
-    if (POL && stop > 0 && st.hops >= stop) break;
+    // the decision, after hop h0 (the hash reset that may follow a hop does
+    // not touch what it reads)
+    if (POL && st.hops >= lim) {
+      if (lim != pc->pol->h0) break;
+      const PolicyOut o = policy_decide(*pc->pol, S, pc->hbuf, cnt, pc->k, pc->est, pc->kind, ls, pc->feat_out,
+                                        pc->forced_q);
+      if (pc->dec_out && lane == 0) { pc->dec_out[0] = o.beam; pc->dec_out[1] = o.stop; pc->dec_out[3] = o.learned; }
+      ls = o.beam;
+      if (cnt > ls) cnt = ls;
+      lim = o.stop > 0 ? o.stop : 0x7FFFFFFF;
+      if (st.hops >= lim) break;
+    }
     const int sel = first_unexpanded(S.bid, cnt, start);
     if (sel < 0) break;
     const uint32_t pid = S.bid[sel];
@@ -584,18 +608,9 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       int r0;
       cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0, S.rank);
       rmin = r0 < rmin ? r0 : rmin;
-      if (POL && r0 < pc->k) last_change = st.hops;
+      if (POL == 2 && r0 < kq) last_change = st.hops;
     }
     start = (sel + 1) < rmin ? (sel + 1) : rmin;
-    if (POL && !decided && pc->pol->mode != JAG_POLICY_PLAIN && st.hops == pc->pol->h0) {
-      const PolicyOut o = policy_decide(*pc->pol, S, pc->hbuf, cnt, pc->k, pc->est, pc->kind, ls0, pc->feat_out,
-                                        pc->forced_q);
-      ls = o.beam;
-      stop = o.stop;
-      learned = o.learned;
-      if (cnt > ls) cnt = ls;
-      decided = true;
-    }
     if (fill > (hsize >> 1) + (hsize >> 2)) {
       __syncwarp();
       for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
@@ -603,9 +618,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       __syncwarp();
     }
   }
-  if (POL && pc->dec_out && lane == 0) {
-    pc->dec_out[0] = ls; pc->dec_out[1] = stop; pc->dec_out[2] = last_change; pc->dec_out[3] = learned;
-  }
+  if (POL == 2 && pc->dec_out && lane == 0) pc->dec_out[2] = last_change;
   return cnt;
 }
 
