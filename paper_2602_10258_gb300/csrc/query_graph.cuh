@@ -31,7 +31,6 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
   const size_t wbytes = warp_smem_bytes(lcap, hbits) + (POL ? kPolicyCtxBytes : 0);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, hbits);
-  PolicyCtx *pcs = reinterpret_cast<PolicyCtx *>(wb + warp_smem_bytes(lcap, hbits));
   const int64_t sample = ix.n < 4096 ? ix.n : 4096;
   for (;;) {
     unsigned long long qi = 0;
@@ -52,12 +51,12 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
                           : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
       // the policy network's scratch: the candidate arrays cid, ck1 (free between hops)
       if (lane == 0)
-        *pcs = PolicyCtx{&pol, est, f.kind, k, reinterpret_cast<float *>(S.cid),
-                         pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr,
-                         pol.decisions ? pol.decisions + (int64_t)qi * 4 : nullptr,
-                         pol.forced ? pol.forced + (int64_t)qi * 2 : nullptr};
+        *policy_ctx(S) = PolicyCtx{&pol, est, f.kind, k, reinterpret_cast<float *>(S.cid),
+                                   pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr,
+                                   pol.decisions ? pol.decisions + (int64_t)qi * 4 : nullptr,
+                                   pol.forced ? pol.forced + (int64_t)qi * 2 : nullptr, 0};
       __syncwarp();
-      cnt = greedy_search<CAP, P, CPL, FMT, POL>(ix, key, q, ls, hbits, S, sink, st, pcs);
+      cnt = greedy_search<CAP, P, CPL, FMT, POL>(ix, key, q, ls, hbits, S, sink, st);
     } else {
       cnt = greedy_search<CAP, P, CPL, FMT, 0>(ix, key, q, ls, hbits, S, sink, st);
     }

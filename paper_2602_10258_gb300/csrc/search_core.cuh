@@ -491,9 +491,9 @@ __device__ __noinline__ static PolicyOut policy_decide(const jag_policy &pol, co
   return o;
 }
 
-// Per-search policy context passed to greedy_search.  It lives in the
-// warp's shared memory (kPolicyCtxBytes after its search arrays), so that the
-// search loop keeps no register for it.
+// Per-search policy context of greedy_search.  It lives in the warp's shared
+// memory, kPolicyCtxBytes right after its search arrays (policy_ctx), so that
+// the search loop keeps no register for it.
 struct PolicyCtx {
   const jag_policy *pol;   // nullptr: plain search
   int64_t est;
@@ -503,27 +503,36 @@ struct PolicyCtx {
   float *feat_out;         // [12] or nullptr
   int32_t *dec_out;        // [4] or nullptr
   const int32_t *forced_q; // [2] or nullptr
+  int32_t lim;             // hop limit of the current phase (set by greedy_search)
 };
 constexpr size_t kPolicyCtxBytes = 64;
 static_assert(sizeof(PolicyCtx) <= kPolicyCtxBytes, "policy context slot");
+
+__device__ __forceinline__ PolicyCtx *policy_ctx(const WarpSmem &S) {
+  return reinterpret_cast<PolicyCtx *>(S.rank + 32);
+}
 
 // Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
 // hold the final list L (count returned).
 // POL: 0 plain search; 1 with the policy's decision at hop h0; 2 as 1, and the
 // trace of the search (decisions and the last hop that changed the first k
-// entries) written to pc->dec_out.
+// entries) written to dec_out; the caller fills policy_ctx(S) first.
 template <int CAP, int P, int CPL, int FMT, int POL = 0, class KeyFn, class Sink>
 __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunks<CPL, FMT> &q, int ls,
-                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st,
-                             const PolicyCtx *pc = nullptr) {
-  // policy state: the hop limit of the current phase -- the decision hop h0,
-  // then the stop hop (>= h0; a stop at h0 ends the search right after the
-  // decision, so a limit equal to h0 is always the decision's) -- and, for a
-  // trace, the last hop that changed the first k entries
-  int lim = (POL && pc->pol->mode != JAG_POLICY_PLAIN) ? pc->pol->h0 : 0x7FFFFFFF;
-  int last_change = 0;
-  const int kq = POL == 2 ? pc->k : 0;
+                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st) {
+  // policy state: the hop limit of the current phase, kept in shared memory
+  // -- the decision hop h0, then the stop hop (>= h0; a stop at h0 ends the
+  // search right after the decision, so a limit equal to h0 is always the
+  // decision's) -- and, for a trace, the last hop that changed the first k
+  // entries
   const int lane = threadIdx.x & 31;
+  int last_change = 0;
+  const int kq = POL == 2 ? policy_ctx(S)->k : 0;
+  if (POL && lane == 0) {
+    PolicyCtx *pc = policy_ctx(S);
+    pc->lim = pc->pol->mode != JAG_POLICY_PLAIN ? pc->pol->h0 : 0x7FFFFFFF;
+    if (pc->dec_out) { pc->dec_out[0] = ls; pc->dec_out[1] = 0; pc->dec_out[2] = 0; pc->dec_out[3] = 0; }
+  }
   const uint32_t hsize = 1u << hbits;
   for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
   __syncwarp();
@@ -540,21 +549,28 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
   __syncwarp();
   int cnt = 1, start = 0;
   st.hops = 0; st.seen = 0; st.dcs = 1;
-  if (POL && pc->feat_out && lane < JAG_MLP_FEATURES) pc->feat_out[lane] = 0.f;
-  if (POL && pc->dec_out && lane == 0) {
-    pc->dec_out[0] = ls; pc->dec_out[1] = 0; pc->dec_out[2] = 0; pc->dec_out[3] = 0;
+  if (POL) {
+    float *fo = policy_ctx(S)->feat_out;
+    if (fo && lane < JAG_MLP_FEATURES) fo[lane] = 0.f;
   }
   for (;;) {
     // the decision, after hop h0 (the hash reset that may follow a hop does
     // not touch what it reads)
-    if (POL && st.hops >= lim) {
-      if (lim != pc->pol->h0) break;
+    if (POL && st.hops >= policy_ctx(S)->lim) {
+      const PolicyCtx *pc = policy_ctx(S);
+      if (pc->lim != pc->pol->h0) break;
       const PolicyOut o = policy_decide(*pc->pol, S, pc->hbuf, cnt, pc->k, pc->est, pc->kind, ls, pc->feat_out,
                                         pc->forced_q);
-      if (pc->dec_out && lane == 0) { pc->dec_out[0] = o.beam; pc->dec_out[1] = o.stop; pc->dec_out[3] = o.learned; }
+      const int lim = o.stop > 0 ? o.stop : 0x7FFFFFFF;
+      __syncwarp();
+      if (lane == 0) {
+        PolicyCtx *pw = policy_ctx(S);
+        if (pw->dec_out) { pw->dec_out[0] = o.beam; pw->dec_out[1] = o.stop; pw->dec_out[3] = o.learned; }
+        pw->lim = lim;
+      }
+      __syncwarp();
       ls = o.beam;
       if (cnt > ls) cnt = ls;
-      lim = o.stop > 0 ? o.stop : 0x7FFFFFFF;
       if (st.hops >= lim) break;
     }
     const int sel = first_unexpanded(S.bid, cnt, start);
@@ -618,7 +634,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       __syncwarp();
     }
   }
-  if (POL == 2 && pc->dec_out && lane == 0) pc->dec_out[2] = last_change;
+  if (POL == 2 && lane == 0 && policy_ctx(S)->dec_out) policy_ctx(S)->dec_out[2] = last_change;
   return cnt;
 }
 

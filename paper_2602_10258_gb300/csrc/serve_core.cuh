@@ -211,7 +211,7 @@ __device__ __forceinline__ void pad_rows(int k, int32_t *oid, float *od) {
 // mapping of the stored rows (format FMT); CPLF: chunks per lane of the fp32
 // rows with 32 lanes per row (the exact scan and the re-rank).
 template <int CAP, int P, int CPL, int FMT, bool POL, int CPLF>
-__device__ void serve_query(const ServeArgs &a, const WarpSmem &S, PolicyCtx *pcs, const jag_filter &f,
+__device__ void serve_query(const ServeArgs &a, const WarpSmem &S, const jag_filter &f,
                             const float *qv, const uint8_t *aux, int64_t aux_bytes, uint8_t *lut_base,
                             int32_t *oid, float *od, uint32_t *status) {
   const int lane = threadIdx.x & 31;
@@ -250,9 +250,10 @@ __device__ void serve_query(const ServeArgs &a, const WarpSmem &S, PolicyCtx *pc
     const int64_t sample = ix.n < 4096 ? ix.n : 4096;
     const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
                         : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
-    if (lane == 0) *pcs = PolicyCtx{&a.pol, est, f.kind, a.k, reinterpret_cast<float *>(S.cid), nullptr, nullptr, nullptr};
+    if (lane == 0)
+      *policy_ctx(S) = PolicyCtx{&a.pol, est, f.kind, a.k, reinterpret_cast<float *>(S.cid), nullptr, nullptr, nullptr, 0};
     __syncwarp();
-    cnt = greedy_search<CAP, P, CPL, FMT, 1>(ix, key, q, a.ls, a.hbits, S, sink, st, pcs);
+    cnt = greedy_search<CAP, P, CPL, FMT, 1>(ix, key, q, a.ls, a.hbits, S, sink, st);
   } else {
     cnt = greedy_search<CAP, P, CPL, FMT, 0>(ix, key, q, a.ls, a.hbits, S, sink, st);
   }
@@ -287,7 +288,6 @@ serve_kernel(const __grid_constant__ ServeArgs a) {
   const size_t wbytes = warp_smem_bytes(lcap, a.hbits) + (POL ? kPolicyCtxBytes : 0);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, a.hbits);
-  PolicyCtx *pcs = reinterpret_cast<PolicyCtx *>(wb + warp_smem_bytes(lcap, a.hbits));
   for (;;) {
     long long c = 0;
     if (lane == 0) c = serve_claim(a);
@@ -301,7 +301,7 @@ serve_kernel(const __grid_constant__ ServeArgs a) {
     const float *qv = reinterpret_cast<const float *>(a.arena + rq.q_off) + i * a.d;
     int32_t *oid = reinterpret_cast<int32_t *>(a.arena + rq.ids_off) + i * a.k;
     float *od = reinterpret_cast<float *>(a.arena + rq.dist_off) + i * a.k;
-    serve_query<CAP, P, CPL, FMT, POL, CPLF>(a, S, pcs, f, qv, a.arena + rq.aux_off, rq.aux_bytes,
+    serve_query<CAP, P, CPL, FMT, POL, CPLF>(a, S, f, qv, a.arena + rq.aux_off, rq.aux_bytes,
                                              a.lut + rq.lut_off, oid, od, a.req_status + slot);
     // answers visible system-wide before the count that may complete the request
     __threadfence_system();
