@@ -434,7 +434,7 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   L.aux = a->filter_aux;
   L.aux_bytes = a->aux_bytes;
   L.nq = a->nq;
-  L.k = a->k; L.ls = a->beam; L.hbits = hb;
+  L.k = a->k; L.ls = a->beam; L.hbits = hb; L.hbits_auto = a->hash_bits == 0;
   L.s0 = s0; L.cap = cap; L.scan_all = scan_all;
   L.out_ids = a->out_ids; L.out_dist = a->out_dist; L.counters = a->counters;
   L.plans = (jag::QueryPlan *)(base + L0.plans);

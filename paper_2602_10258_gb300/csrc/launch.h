@@ -18,6 +18,7 @@ struct SearchLaunch {
   int64_t aux_bytes;
   int64_t nq;
   int32_t k, ls, hbits;
+  int32_t hbits_auto;      // hbits is the default: the graph launch may lower it
   int64_t s0, cap;
   int32_t scan_all;
   int32_t *out_ids;

@@ -110,6 +110,7 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   L.nq = nq;
   L.k = a->k; L.ls = a->beam;
   L.hbits = a->hash_bits ? a->hash_bits : 10;
+  L.hbits_auto = a->hash_bits == 0;
   L.s0 = s0; L.cap = cap; L.scan_all = scan_all;
   L.out_ids = a->out_ids; L.out_dist = a->out_dist; L.counters = a->counters;
   L.plans = (QueryPlan *)(base + o_plans);
