@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10=0.95 per selectivity band; plain FP32 vs BF16+learned; p99 ms"
-BEAMS = [16, 24, 32, 48, 64, 96, 128, 192, 256]
+BEAMS = [16, 24, 32, 48, 64, 96, 128, 160, 176, 192, 224, 256]
 BANDS = [(0.0, 1e-4, "<1e-4"), (1e-4, 1e-3, "[1e-4,1e-3)"), (1e-3, 1e-2, "[1e-3,1e-2)"),
          (1e-2, 1e-1, "[1e-2,1e-1)"), (1e-1, 1.01, "[1e-1,1]")]
 K = 10
@@ -41,7 +41,7 @@ R = 32
 LB = 64
 THRESHOLDS = (100, 0)
 ALPHA = 1.2
-S0 = 10000
+S0 = 8192          # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
 SCAN_CAP = 8192
 
 
