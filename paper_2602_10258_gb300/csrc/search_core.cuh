@@ -75,18 +75,21 @@ __device__ __forceinline__ int first_unexpanded(const uint32_t *bid, int cnt, in
 }
 
 // Visited-set probe (two slots, linear); returns true if id was not
-// recorded (new, or not stored because both slots hold other ids).
-__device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t id, bool &inserted) {
+// recorded.  The set forgets: when both slots hold other ids, id replaces the
+// first, so the set keeps mostly recent ids (a slot, once filled, is never
+// empty again, so an id stored in the second slot is still found there).  A
+// forgotten id only costs a recomputed distance: the list drops a repeat, and
+// a vertex that left a full list cannot re-enter it.
+__device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t id) {
   const uint32_t mask = (1u << hbits) - 1;
   const uint32_t h = (id * 0x9E3779B1u) >> (32 - hbits);
   uint32_t old = atomicCAS(&tab[h], kEmptySlot, id);
-  inserted = old == kEmptySlot;
+  if (old == kEmptySlot) return true;
   if (old == id) return false;
-  if (!inserted) {
-    old = atomicCAS(&tab[(h + 1) & mask], kEmptySlot, id);
-    inserted = old == kEmptySlot;
-    if (old == id) return false;
-  }
+  old = atomicCAS(&tab[(h + 1) & mask], kEmptySlot, id);
+  if (old == kEmptySlot) return true;
+  if (old == id) return false;
+  atomicExch(&tab[h], id);
   return true;
 }
 
@@ -536,7 +539,6 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
   const uint32_t hsize = 1u << hbits;
   for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
   __syncwarp();
-  uint32_t fill = 1;
   const int32_t s = ix.entry;
   if (lane == 0) { S.cid[0] = (uint32_t)s; S.hash[((uint32_t)s * 0x9E3779B1u) >> (32 - hbits)] = (uint32_t)s; }
   __syncwarp();
@@ -554,8 +556,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
     if (fo && lane < JAG_MLP_FEATURES) fo[lane] = 0.f;
   }
   for (;;) {
-    // the decision, after hop h0 (the hash reset that may follow a hop does
-    // not touch what it reads)
+    // the decision, after hop h0
     if (POL && st.hops >= policy_ctx(S)->lim) {
       const PolicyCtx *pc = policy_ctx(S);
       if (pc->lim != pc->pol->h0) break;
@@ -599,9 +600,8 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
         k1 = KeyFn::kEdgeAttr ? key1.from_word(aw) : key1(ix, u);
         cand = KeyFn::kScalar || !(full && k1 > (uint32_t)(tkey >> 32));
       }
-      bool inserted = false, keep = false;
-      if (cand) keep = visit_insert(S.hash, hbits, (uint32_t)u, inserted);
-      fill += __popc(__ballot_sync(kFull, inserted));
+      bool keep = false;
+      if (cand) keep = visit_insert(S.hash, hbits, (uint32_t)u);
       st.seen += __popc(__ballot_sync(kFull, keep));
       const uint32_t km = __ballot_sync(kFull, keep);
       const int nc = __popc(km);
@@ -627,12 +627,6 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       if (POL == 2 && r0 < kq) last_change = st.hops;
     }
     start = (sel + 1) < rmin ? (sel + 1) : rmin;
-    if (fill > (hsize >> 1) + (hsize >> 2)) {
-      __syncwarp();
-      for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
-      fill = 0;
-      __syncwarp();
-    }
   }
   if (POL == 2 && lane == 0 && policy_ctx(S)->dec_out) policy_ctx(S)->dec_out[2] = last_change;
   return cnt;
