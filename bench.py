@@ -356,7 +356,7 @@ def run_ours(args):
     serving = None
     if not args.no_serve:
         serving = measure_serving(jag, idx, w, chosen, band, gt_ids, gt_d)
-        log("serving: %s" % {k: (v["p50_ms"], v["p99_ms"], v["achieved_qps"]) for k, v in serving.items()})
+        log("serving: %s" % {k: (v["p50_ms"], v["p99_ms"], v["achieved_qps"]) for k, v in serving.items() if isinstance(v, dict)})
 
     cpu, ocnt = None, None
     if rank == 0 and not args.no_cpu:
