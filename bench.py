@@ -355,7 +355,7 @@ def run_ours(args):
         log("bf16+learned: %s" % {k: v for k, v in forms["bf16_learned"].items() if k in ("beam", "stop_scale", "qps")})
     serving = None
     if not args.no_serve:
-        serving = measure_serving(jag, idx, w, chosen, band, gt_ids, gt_d)
+        serving = measure_serving(jag, idx, w, chosen, band, gt_ids, gt_d, value / world)
         log("serving: %s" % {k: (v["p50_ms"], v["p99_ms"], v["achieved_qps"]) for k, v in serving.items() if isinstance(v, dict)})
 
     cpu, ocnt = None, None
@@ -537,26 +537,28 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
             "steps": steps}
 
 
-def serve_saturation(jag, idx, w, beam, n_req=2000):
-    """Throughput of the serve loop with every request of the mix (sizes
-    uniform in 1..256 queries) submitted at once: its saturated QPS."""
+def serve_saturation(jag, idx, w, beam, batch_qps, n_req=2000):
+    """Saturated throughput of the serve loop: the QPS it achieves under
+    Poisson arrivals of the request mix (sizes uniform in 1..256 queries)
+    offered at 1.5x the batch path's QPS."""
     rng = np.random.default_rng(1)
     sizes = rng.integers(1, 257, n_req).astype(np.int32)
     first = np.array([rng.integers(0, len(w.q) - s + 1) for s in sizes], np.int64)
+    arrival = np.cumsum(rng.exponential(float(sizes.mean()) / (1.5 * batch_qps), n_req))
     srv = jag.Server(idx, K, beam, s0=S0, scan_cap=SCAN_CAP, max_queries=1 << 17)
     t1 = time.perf_counter()
-    srv.replay(np.zeros(n_req), sizes, first, w.q, w.filters, w.aux, timeout_s=300.0)
+    srv.replay(arrival, sizes, first, w.q, w.filters, w.aux, timeout_s=300.0)
     wall = time.perf_counter() - t1
     srv.stop()
     return float(sizes.sum()) / wall
 
 
-def measure_serving(jag, idx, w, beam, band, gt_ids, gt_d, n_req=2000, loads=(0.5, 0.8)):
+def measure_serving(jag, idx, w, beam, band, gt_ids, gt_d, batch_qps, n_req=2000, loads=(0.5, 0.8)):
     """The serve loop under open-loop Poisson arrivals: request sizes uniform
     in 1..256 queries (rows of the 10,000-query batch), arrival rate a
     fraction of the loop's own saturated throughput; p50 / p99 latency from
     arrival to completion, achieved QPS, and recall per band."""
-    sat_qps = serve_saturation(jag, idx, w, beam)
+    sat_qps = serve_saturation(jag, idx, w, beam, batch_qps)
     out = {"saturated_qps": round(sat_qps, 1)}
     rng = np.random.default_rng(0)
     for load in loads:
@@ -748,7 +750,7 @@ def run_serve_large(args):
     qps = nq / (ms / 1000.0)
     gt_all = np.concatenate([gt, np.full((nq - ns, K), -1, np.int32)])
     gd_all = np.concatenate([gd, np.full((nq - ns, K), np.inf, np.float32)])
-    serving = measure_serving(jag, idx, w, chosen, band, gt_all, gd_all)
+    serving = measure_serving(jag, idx, w, chosen, band, gt_all, gd_all, qps)
     idx.close()
     out = {"mode": "serve_large", "metric": METRIC, "unit": "queries/s", "dtype": "bf16 rows, f32 re-rank",
            "data": "synthetic",
