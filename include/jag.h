@@ -185,7 +185,11 @@ typedef struct jag_search_args {
   int32_t *counters;           /* optional [nq][4] int32: hops, first-seen
                                   neighbours, distance computations, routed    */
   int32_t flags;               /* JAG_SEARCH_* bits                            */
-  int32_t hash_bits;           /* log2 slots of the visited set, 0 = default   */
+  int32_t hash_bits;           /* log2 slots of the visited set, in [5, 16];
+                                  0 = default: 10, or 9 where that lets the
+                                  graph kernel reach its blocks per SM.  The
+                                  set only saves recomputed distances: answers
+                                  do not depend on its size                    */
   void *ev_graph_begin;        /* optional cudaEvent_t recorded just before
                                   the graph-search kernel                      */
   void *ev_graph_end;          /* ... and just after it                        */
