@@ -133,6 +133,16 @@ static cudaError_t launch_graph_cap(const SearchLaunch &L, int P, int CPL) {
 }
 
 template <int FMT>
+static cudaError_t launch_graph_fmt_plain(const SearchLaunch &L, int P, int CPL) {
+  switch (list_capacity(L.ls)) {
+    case 64: return launch_graph_cap<64, FMT, 0>(L, P, CPL);
+    case 128: return launch_graph_cap<128, FMT, 0>(L, P, CPL);
+    case 256: return launch_graph_cap<256, FMT, 0>(L, P, CPL);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int FMT>
 cudaError_t launch_graph_fmt(const SearchLaunch &L) {
   int P, CPL;
   const int nch = FMT == JAG_VEC_F32 ? L.ix.nchunks : L.ix.qchunks;
@@ -143,15 +153,12 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L) {
   if (L.has_policy) {
     // traces (decisions written) take the capacity-256 kernel for any beam
     if (L.policy.decisions) return launch_graph_cap<256, FMT, 2>(L, P, CPL);
+    // the plain mode without features is the plain search
+    if (L.policy.mode == JAG_POLICY_PLAIN && !L.policy.features) return launch_graph_fmt_plain<FMT>(L, P, CPL);
     if (list_capacity(L.ls) <= 128) return launch_graph_cap<128, FMT, 1>(L, P, CPL);
     return launch_graph_cap<256, FMT, 1>(L, P, CPL);
   }
-  switch (list_capacity(L.ls)) {
-    case 64: return launch_graph_cap<64, FMT, 0>(L, P, CPL);
-    case 128: return launch_graph_cap<128, FMT, 0>(L, P, CPL);
-    case 256: return launch_graph_cap<256, FMT, 0>(L, P, CPL);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_graph_fmt_plain<FMT>(L, P, CPL);
 }
 
 }  // namespace jag

@@ -109,6 +109,40 @@ def test_learned_policy_parity(case, tau, seed, scale, storage):
     gi.close()
 
 
+@pytest.mark.parametrize("tau,seed,scale,h0", [(0.0, 3, 64.0, 5), (0.4, 4, 48.0, 1), (0.0, 6, 0.0, 7),
+                                               (0.0, 7, 64.0, 300)])
+@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("want_features", [False, True])
+def test_learned_policy_without_trace(case, tau, seed, scale, h0, storage, want_features):
+    """Without a trace (no decisions requested) the policy search takes the
+    kernel that does not track the last change of the first k entries;
+    answers, hop counts and features are the oracle's (h0 = 300 lies past
+    every search's end)."""
+    w, ix = case
+    nq = len(w.q)
+    theta = M.init_params(NL, seed=seed)
+    theta[-1] = 0.5
+    theta = theta.astype(np.float32)
+    k, ls = 10, 160
+    oix = ix if storage == 0 else O.Index.from_workload(w, R=ix.R, graph=ix.graph, entry=ix.entry, storage=storage)
+    opol = O.Policy(O.POL_LEARNED, h0=h0, theta=theta, ladder=LADDER, tau=tau, stop_scale=scale, nq=nq,
+                    want_features=True, want_decisions=True)
+    oi, od, oc = O.query_policy(oix, w.q, w.filters, w.aux, k, ls, opol)
+    gi = _gpu_index(w, ix, storage)
+    feats = torch.full((nq, 12), 7.0, dtype=torch.float32, device="cuda") if want_features else None
+    gpol = jag.Policy.learned(torch.from_numpy(theta).cuda(), ladder=LADDER, h0=h0, tau=tau, stop_scale=scale,
+                              features=feats)
+    gids, gd, gc = _gpu_policy_search(gi, w, k, ls, gpol)
+    assert (gids == oi).all(), np.nonzero(~(gids == oi).all(1))[0][:5]
+    assert np.array_equal(gd.view(np.uint32), od.view(np.uint32))
+    assert (gc[:, 0] == oc[:, 0]).all()
+    if want_features:
+        assert np.array_equal(feats.cpu().numpy().view(np.uint32), opol.features.view(np.uint32))
+    if h0 < 100 and scale > 0 and tau == 0.0:
+        assert (opol.decisions[:, 1] > 0).any()      # some searches stop early
+    gi.close()
+
+
 def test_policy_plain_mode_is_the_plain_search(case):
     w, ix = case
     gi = _gpu_index(w, ix)
