@@ -18,17 +18,23 @@ namespace jag {
 // row is 32 chunks).
 constexpr int kGraphLanes = 32;
 
-// Blocks per SM the graph kernel is compiled for (its register budget): one
-// row chunk per lane -- 8 (64 registers); the plain search of FP8 rows, whose
-// 8-lane rows leave registers to spare, 9 (56 registers), measured faster on
-// the 128-d label workload than 8 or 10; wider rows, 1.
+// Warps (searches) per CTA of the graph kernel: 2 for the plain search, so
+// that CTAs leave an SM in finer steps during the last wave and the exact
+// scan's CTAs fit sooner; 4 with a policy, whose 64 extra bytes of shared
+// memory per warp would otherwise cost a CTA per SM.
+__host__ __device__ constexpr int graph_warps(int POL) { return POL ? 4 : 2; }
+
+// CTAs per SM the graph kernel is compiled for (its register budget): one
+// row chunk per lane -- 32 warps (64 registers); the plain search of FP8 rows,
+// whose 8-lane rows leave registers to spare, 36 warps (56 registers),
+// measured faster on the 128-d label workload than 32 or 40; wider rows, 1.
 __host__ __device__ constexpr int graph_min_blocks(int CPL, int FMT, int POL) {
-  return CPL != 1 ? 1 : (FMT == JAG_VEC_FP8 && POL == 0 ? 9 : 8);
+  return CPL != 1 ? 1 : (FMT == JAG_VEC_FP8 && POL == 0 ? 36 : 32) / graph_warps(POL);
 }
 
 // POL: 0 plain, 1 with the search policy, 2 with the policy and its trace.
 template <int CAP, int P, int CPL, int FMT, int POL>
-__global__ void __launch_bounds__(kSearchWarps * 32, graph_min_blocks(CPL, FMT, POL))
+__global__ void __launch_bounds__(graph_warps(POL) * 32, graph_min_blocks(CPL, FMT, POL))
 query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
              const uint8_t *lut_base, int64_t nq, int k, int ls, int hbits, int rr, int32_t *rr_ids,
              int32_t *out_ids, float *out_dist, int32_t *counters, unsigned long long *work,
@@ -88,25 +94,26 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
 template <int CAP, int P, int CPL, int FMT, int POL>
 static cudaError_t launch_graph_one(const SearchLaunch &L) {
   const int lcap = list_slots(L.ls);
+  constexpr int kGraphWarps = graph_warps(POL);
   auto kern = query_kernel<CAP, P, CPL, FMT, POL>;
   // The default visited set (2^10 slots) shrinks to 2^9 when that brings the
   // blocks per SM up to the number the kernel is compiled for; the set only
   // saves recomputation, answers do not depend on its size.
   int hbits = L.hbits;
   auto smem_of = [&](int hb) {
-    return (size_t)kSearchWarps * (warp_smem_bytes(lcap, hb) + (POL ? kPolicyCtxBytes : 0));
+    return (size_t)kGraphWarps * (warp_smem_bytes(lcap, hb) + (POL ? kPolicyCtxBytes : 0));
   };
-  int bps = blocks_per_sm(kern, smem_of(hbits));
+  int bps = blocks_per_sm(kern, smem_of(hbits), kGraphWarps);
   if (L.hbits_auto && hbits > 9 && bps < graph_min_blocks(CPL, FMT, POL)) {
-    const int b9 = blocks_per_sm(kern, smem_of(9));
+    const int b9 = blocks_per_sm(kern, smem_of(9), kGraphWarps);
     if (b9 > bps) { hbits = 9; bps = b9; }
   }
   const size_t smem = smem_of(hbits);
   if (bps == 0) return cudaErrorInvalidConfiguration;
-  const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
+  const int64_t want = std::max<int64_t>((L.nq + kGraphWarps - 1) / kGraphWarps, 1);
   const int64_t grid = std::min<int64_t>((int64_t)bps * num_sms(), want);
   if (L.ev_begin) cudaEventRecord(L.ev_begin, L.stream);
-  kern<<<(unsigned)grid, kSearchWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lut,
+  kern<<<(unsigned)grid, kGraphWarps * 32, smem, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lut,
                                                              L.nq, L.k, L.ls, hbits, L.rr, L.rr_ids, L.out_ids,
                                                              L.out_dist, L.counters, L.work, L.policy);
   if (L.ev_end) cudaEventRecord(L.ev_end, L.stream);
