@@ -180,8 +180,12 @@ __device__ __forceinline__ void routed_candidates(const DevIndex &ix, const jag_
 // filters, the gathered list for subset and boolean ones), stages its rows
 // in shared memory round by round, and leaves the tile's top k in a partial
 // list; merge_scan_kernel combines a query's partial lists.
+// Warps per CTA of the exact scan: two, so that a scan CTA fits on an SM as
+// soon as little of the graph search's last wave has left it.
+constexpr int kScanWarps = 2;
+
 template <int CAP, int P, int CPL>
-__global__ void __launch_bounds__(kSearchWarps * 32)
+__global__ void __launch_bounds__(kScanWarps * 32)
 scan_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
                  const int32_t *lists, int64_t cap, int k, int64_t tile, int ntiles, int rpr, const uint64_t *items,
                  const unsigned long long *nitems, unsigned long long *work, uint64_t *part_key,
@@ -530,18 +534,18 @@ static cudaError_t launch_scan(const SearchLaunch &L) {
   const int64_t want = std::max<int64_t>((L.nq + kSearchWarps - 1) / kSearchWarps, 1);
   // the exact scan for the routed queries (k <= ls <= CAP)
   const int rpr = scan_rows_per_round(L.ix.xs);
-  const size_t ssm = (size_t)kSearchWarps * (warp_smem_bytes(list_slots(L.k), 5) + 32 * 4 + 2 * (size_t)rpr * L.ix.xs * 4);
+  const size_t ssm = (size_t)kScanWarps * (warp_smem_bytes(list_slots(L.k), 5) + 32 * 4 + 2 * (size_t)rpr * L.ix.xs * 4);
   auto sk = scan_tile_kernel<CAP, P, CPL>;
   // items live after the partial lists' id array; counters in work[2..3]
   uint64_t *items = reinterpret_cast<uint64_t *>(L.part_id + (size_t)std::max<int64_t>(L.nq, 1) * L.ntiles * L.k);
   items = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(items) + 255) & ~uintptr_t(255));
   scan_items_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.ix, L.filters, L.plans, L.lists, L.cap,
                                                                           L.nq, L.tile, items, L.work + 3);
-  const int sbps = blocks_per_sm(sk, ssm);
+  const int sbps = blocks_per_sm(sk, ssm, kScanWarps);
   if (sbps == 0) return cudaErrorInvalidConfiguration;
   const int64_t sgrid = std::min<int64_t>((int64_t)sbps * num_sms(),
-                                          std::max<int64_t>(1, (L.nq * L.ntiles + kSearchWarps - 1) / kSearchWarps));
-  sk<<<(unsigned)sgrid, kSearchWarps * 32, ssm, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap,
+                                          std::max<int64_t>(1, (L.nq * L.ntiles + kScanWarps - 1) / kScanWarps));
+  sk<<<(unsigned)sgrid, kScanWarps * 32, ssm, L.stream>>>(L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap,
                                                            L.k, L.tile, L.ntiles, rpr, items, L.work + 3, L.work + 2,
                                                            L.part_key, L.part_id);
   const size_t msm = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.k), 5);
