@@ -499,10 +499,10 @@ void scan_tiling(int64_t n, int scan_all, int64_t s0, int64_t cap, int32_t *ntil
 }
 
 // Rows per round of the staged scan: two rounds of rows (double buffer)
-// take 8 KB of shared memory per warp, so that a scan block (4 warps) fits
-// beside the graph kernel as soon as two of its blocks have left an SM --
-// the scan then runs inside the graph search's last wave.  (16 KB per warp:
-// 3.32 M against 3.59 M QPS on the 1M label batch.)
+// take 8 KB of shared memory per warp, so that a scan CTA fits beside the
+// graph kernel as soon as a few of its warps have left an SM -- the scan then
+// runs inside the graph search's last wave.  (16 KB per warp: 3.32 M against
+// 3.59 M QPS on the 1M label batch; 4 KB: within 1 %.)
 int scan_rows_per_round(int64_t xs) {
   const int64_t r = 4096 / (xs * 4);
   return (int)std::max<int64_t>(1, std::min<int64_t>(32, r));

@@ -33,7 +33,7 @@
 
 namespace jag {
 
-constexpr int kSearchWarps = 4;   // warps (searches) per CTA
+constexpr int kSearchWarps = 4;   // warps (searches) per CTA of the search kernels (the graph kernel: graph_warps)
 
 // Shared-memory slice of one warp.
 struct WarpSmem {
