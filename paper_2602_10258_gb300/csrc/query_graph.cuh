@@ -22,7 +22,7 @@ constexpr int kGraphLanes = 32;
 // that CTAs leave an SM in finer steps during the last wave and the exact
 // scan's CTAs fit sooner; 4 with a policy, whose 64 extra bytes of shared
 // memory per warp would otherwise cost a CTA per SM.
-__host__ __device__ constexpr int graph_warps(int POL) { return POL ? 4 : 2; }
+__host__ __device__ constexpr int graph_warps(int POL) { return POL == 2 ? 4 : 2; }
 
 // CTAs per SM the graph kernel is compiled for (its register budget): one
 // row chunk per lane -- 32 warps (64 registers); the plain search of FP8 rows,
@@ -42,7 +42,7 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(ls);
-  const size_t wbytes = warp_smem_bytes(lcap, hbits) + (POL ? kPolicyCtxBytes : 0);
+  const size_t wbytes = warp_smem_bytes(lcap, hbits) + (POL == 2 ? kPolicyCtxBytes : 0);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, hbits);
   const int64_t sample = ix.n < 4096 ? ix.n : 4096;
@@ -60,7 +60,31 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
     NoSink sink;
     SearchStats st;
     int cnt;
-    if constexpr (POL) {
+    if constexpr (POL == 1) {
+      // the plain search loop up to hop h0, the decision outside it, then the
+      // same loop again from where it stopped (one inlined copy of the loop)
+      const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
+                          : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
+      float *fo = pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr;
+      if (fo && lane < JAG_MLP_FEATURES) fo[lane] = 0.f;
+      SearchCursor cur{0, 0};
+      int lsq = ls, lim = pol.mode != JAG_POLICY_PLAIN ? pol.h0 : 0x7FFFFFFF;
+      bool decided = false;
+      for (;;) {
+        cnt = greedy_search<CAP, P, CPL, FMT, 0, true>(ix, key, q, lsq, hbits, S, sink, st, lim, &cur);
+        if (decided || st.hops < lim) break;
+        __syncwarp();
+        const PolicyOut o = policy_decide(pol, S, reinterpret_cast<float *>(S.cid), cnt, k, est, f.kind, ls, fo,
+                                          pol.forced ? pol.forced + (int64_t)qi * 2 : nullptr);
+        __syncwarp();
+        decided = true;
+        lsq = o.beam;
+        if (cnt > lsq) cnt = lsq;
+        if (o.stop > 0 && st.hops >= o.stop) break;
+        lim = o.stop > 0 ? o.stop : 0x7FFFFFFF;
+        cur.cnt = cnt;
+      }
+    } else if constexpr (POL == 2) {
       const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
                           : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
       // the policy network's scratch: the candidate arrays cid, ck1 (free between hops)
@@ -101,7 +125,7 @@ static cudaError_t launch_graph_one(const SearchLaunch &L) {
   // saves recomputation, answers do not depend on its size.
   int hbits = L.hbits;
   auto smem_of = [&](int hb) {
-    return (size_t)kGraphWarps * (warp_smem_bytes(lcap, hb) + (POL ? kPolicyCtxBytes : 0));
+    return (size_t)kGraphWarps * (warp_smem_bytes(lcap, hb) + (POL == 2 ? kPolicyCtxBytes : 0));
   };
   int bps = blocks_per_sm(kern, smem_of(hbits), kGraphWarps);
   if (L.hbits_auto && hbits > 9 && bps < graph_min_blocks(CPL, FMT, POL)) {

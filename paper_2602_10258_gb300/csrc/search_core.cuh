@@ -515,14 +515,25 @@ __device__ __forceinline__ PolicyCtx *policy_ctx(const WarpSmem &S) {
   return reinterpret_cast<PolicyCtx *>(S.rank + 32);
 }
 
+// Where a search stands between two calls of greedy_search: the count of L
+// and the first position that may hold an unexpanded entry.
+struct SearchCursor {
+  int cnt, start;
+};
+
 // Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
 // hold the final list L (count returned).
 // POL: 0 plain search; 1 with the policy's decision at hop h0; 2 as 1, and the
 // trace of the search (decisions and the last hop that changed the first k
 // entries) written to dec_out; the caller fills policy_ctx(S) first.
-template <int CAP, int P, int CPL, int FMT, int POL = 0, class KeyFn, class Sink>
+// RES: the search stops before a hop once st.hops >= max_hops, and ends by
+// storing its cursor in *cur; if cur->cnt > 0 on entry it resumes instead of
+// starting (L, the visited set and st are then as the stopped search left
+// them).  Without RES both arguments are ignored.
+template <int CAP, int P, int CPL, int FMT, int POL = 0, bool RES = false, class KeyFn, class Sink>
 __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunks<CPL, FMT> &q, int ls,
-                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st) {
+                             int hbits, const WarpSmem &S, Sink &sink, SearchStats &st,
+                             int max_hops = 0x7FFFFFFF, SearchCursor *cur = nullptr) {
   // policy state: the hop limit of the current phase, kept in shared memory
   // -- the decision hop h0, then the stop hop (>= h0; a stop at h0 ends the
   // search right after the decision, so a limit equal to h0 is always the
@@ -536,21 +547,25 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
     pc->lim = pc->pol->mode != JAG_POLICY_PLAIN ? pc->pol->h0 : 0x7FFFFFFF;
     if (pc->dec_out) { pc->dec_out[0] = ls; pc->dec_out[1] = 0; pc->dec_out[2] = 0; pc->dec_out[3] = 0; }
   }
-  const uint32_t hsize = 1u << hbits;
-  for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
-  __syncwarp();
-  const int32_t s = ix.entry;
-  if (lane == 0) { S.cid[0] = (uint32_t)s; S.hash[((uint32_t)s * 0x9E3779B1u) >> (32 - hbits)] = (uint32_t)s; }
-  __syncwarp();
-  {
+  const bool resume = RES && cur->cnt > 0;
+  int cnt = 1, start = 0;
+  if (resume) {
+    cnt = cur->cnt;
+    start = cur->start;
+  } else {
+    const uint32_t hsize = 1u << hbits;
+    for (uint32_t i = lane; i < hsize; i += 32) S.hash[i] = kEmptySlot;
+    __syncwarp();
+    const int32_t s = ix.entry;
+    if (lane == 0) { S.cid[0] = (uint32_t)s; S.hash[((uint32_t)s * 0x9E3779B1u) >> (32 - hbits)] = (uint32_t)s; }
+    __syncwarp();
     const float d0 = candidate_distances<P, CPL, 4, FMT>(ix, q, S.cid, 1);
     const uint32_t k0 = key1(ix, s);
     const float d0b = __shfl_sync(kFull, d0, 0);
     if (lane == 0) { S.bkey[0] = key1.key(k0, d0b); S.bid[0] = (uint32_t)s; }
+    __syncwarp();
+    st.hops = 0; st.seen = 0; st.dcs = 1;
   }
-  __syncwarp();
-  int cnt = 1, start = 0;
-  st.hops = 0; st.seen = 0; st.dcs = 1;
   if (POL) {
     float *fo = policy_ctx(S)->feat_out;
     if (fo && lane < JAG_MLP_FEATURES) fo[lane] = 0.f;
@@ -574,6 +589,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       if (cnt > ls) cnt = ls;
       if (st.hops >= lim) break;
     }
+    if (RES && st.hops >= max_hops) break;
     const int sel = first_unexpanded(S.bid, cnt, start);
     if (sel < 0) break;
     const uint32_t pid = S.bid[sel];
@@ -629,6 +645,7 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
     start = (sel + 1) < rmin ? (sel + 1) : rmin;
   }
   if (POL == 2 && lane == 0 && policy_ctx(S)->dec_out) policy_ctx(S)->dec_out[2] = last_change;
+  if (RES) { cur->cnt = cnt; cur->start = start; }
   return cnt;
 }
 
