@@ -18,10 +18,10 @@ namespace jag {
 // row is 32 chunks).
 constexpr int kGraphLanes = 32;
 
-// Warps (searches) per CTA of the graph kernel: 2 for the plain search, so
-// that CTAs leave an SM in finer steps during the last wave and the exact
-// scan's CTAs fit sooner; 4 with a policy, whose 64 extra bytes of shared
-// memory per warp would otherwise cost a CTA per SM.
+// Warps (searches) per CTA of the graph kernel: 2, so that CTAs leave an SM
+// in finer steps during the last wave and the exact scan's CTAs fit sooner;
+// 4 for a traced policy search, whose 64-byte policy context per warp would
+// otherwise cost a CTA per SM.
 __host__ __device__ constexpr int graph_warps(int POL) { return POL == 2 ? 4 : 2; }
 
 // CTAs per SM the graph kernel is compiled for (its register budget): one
@@ -62,7 +62,9 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
     int cnt;
     if constexpr (POL == 1) {
       // the plain search loop up to hop h0, the decision outside it, then the
-      // same loop again from where it stopped (one inlined copy of the loop)
+      // same loop again from where it stopped (one inlined copy of the loop,
+      // no call inside it); the network's scratch is the candidate arrays
+      // cid, ck1, free between hops
       const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
                           : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
       float *fo = pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr;
