@@ -1,8 +1,8 @@
 """Parity at full size: the label workload the benchmark times (N=1,000,000,
 d=128, 10,000 queries, k=10, R=32, thresholds {100%, 0%}) in the benchmark's
-launch configurations: one jag_search over the whole batch with s0 = 10,000
-at the beams the benchmark measures -- FP32 at 192, BF16 at 192, FP8 at 256,
-and BF16 with a beam / stop policy at base beam 256.
+launch configurations: one jag_search over the whole batch with s0 = 8,192
+at the beams the benchmark measures -- FP32 at 192, BF16 at 192, FP8 at 224,
+and BF16 with a beam / stop policy at base beam 192.
 
 The oracle cannot rebuild a 1M-point graph inside a test, so the graph here
 comes from the GPU build, whose output equals the oracle build bit for bit at
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 jag = pytest.importorskip("paper_2602_10258_gb300.jag")
 
-N, NQ, K, BEAM, S0, CAP = 1_000_000, 10_000, 10, 192, 10_000, 8192
+N, NQ, K, BEAM, S0, CAP = 1_000_000, 10_000, 10, 192, 8192, 8192
 
 
 @pytest.fixture(scope="module")
@@ -98,7 +98,7 @@ def test_recall_against_brute_force_sample(full):
     assert (rec[cnt[sample, 3] == 1] == 1.0).all()
 
 
-@pytest.mark.parametrize("fmt,beam", [(1, 192), (2, 256)])
+@pytest.mark.parametrize("fmt,beam", [(1, 192), (2, 224)])
 def test_low_precision_forms_match_oracle(full, fmt, beam):
     """BF16 / FP8 rows on the same graph, at the beams the benchmark times."""
     w, gi, ox, graph, *_ = full
@@ -117,31 +117,35 @@ def test_low_precision_forms_match_oracle(full, fmt, beam):
     assert np.array_equal(dist[sample].view(np.uint32), rd.view(np.uint32))
 
 
-def test_policy_form_matches_oracle(full):
+@pytest.mark.parametrize("trace", [False, True])
+def test_policy_form_matches_oracle(full, trace):
     """BF16 rows with a beam / stop network at the benchmark's policy settings
-    (base beam 256, decision after 32 hops, stop scale 128): decisions and
-    answers equal the oracle's on sampled queries."""
+    (base beam 192, decision after 32 hops, stop scale 192), with and without
+    a trace (the benchmark's form writes none): answers, and decisions where
+    written, equal the oracle's on sampled queries."""
     from oracle import jag_mlp as M
     w, gi, ox, graph, *_ = full
     info = gi.info()
     nl = len(jag.LADDER)
     theta = M.init_params(nl, seed=21)
-    theta[-1] = 2.0                       # stop output near 2 * 128 hops
+    theta[-1] = 1.0                       # stop output near 192 hops
     theta = theta.astype(np.float32)
     fi = jag.Index.from_workload(w, R=32, graph=graph, entry=info["entry"], storage=1)
-    dec = torch.zeros((NQ, 4), dtype=torch.int32, device="cuda")
-    pol = jag.Policy.learned(torch.from_numpy(theta).cuda(), h0=32, tau=0.0, stop_scale=128.0, decisions=dec)
+    dec = torch.zeros((NQ, 4), dtype=torch.int32, device="cuda") if trace else None
+    pol = jag.Policy.learned(torch.from_numpy(theta).cuda(), h0=32, tau=0.0, stop_scale=192.0, decisions=dec)
     q = torch.from_numpy(w.q).cuda()
-    ids, dist, _ = fi.search(q, w.filters, w.aux, K, 256, s0=S0, scan_cap=CAP, policy=pol)
+    ids, dist, _ = fi.search(q, w.filters, w.aux, K, 192, s0=S0, scan_cap=CAP, policy=pol)
     torch.cuda.synchronize()
-    ids, dist, dec = ids.cpu().numpy(), dist.cpu().numpy(), dec.cpu().numpy()
+    ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
     fi.close()
     qx = O.Index.from_workload(w, R=32, graph=graph, entry=info["entry"], storage=1)
     sample = np.random.default_rng(17).choice(NQ, 32, replace=False)
-    opol = O.Policy(O.POL_LEARNED, h0=32, theta=theta, tau=0.0, stop_scale=128.0, nq=len(sample),
+    opol = O.Policy(O.POL_LEARNED, h0=32, theta=theta, tau=0.0, stop_scale=192.0, nq=len(sample),
                     want_decisions=True)
-    rid, rd, rc = O.query_policy(qx, w.q[sample], w.filters[sample], w.aux, K, 256, opol, s0=S0, scan_cap=CAP)
+    rid, rd, rc = O.query_policy(qx, w.q[sample], w.filters[sample], w.aux, K, 192, opol, s0=S0, scan_cap=CAP)
     graph_q = rc[:, 3] == 0
     assert (ids[sample] == rid).all() and np.array_equal(dist[sample].view(np.uint32), rd.view(np.uint32))
-    assert (dec[sample][graph_q] == opol.decisions[graph_q]).all()
-    assert (opol.decisions[graph_q, 1] > 0).any()        # stop hops were set
+    if trace:
+        assert (dec.cpu().numpy()[sample][graph_q] == opol.decisions[graph_q]).all()
+    # some searches end at their stop hop
+    assert (rc[graph_q, 0] == opol.decisions[graph_q, 1]).any()
