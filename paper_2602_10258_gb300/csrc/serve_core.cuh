@@ -250,10 +250,25 @@ __device__ void serve_query(const ServeArgs &a, const WarpSmem &S, const jag_fil
     const int64_t sample = ix.n < 4096 ? ix.n : 4096;
     const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
                         : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
-    if (lane == 0)
-      *policy_ctx(S) = PolicyCtx{&a.pol, est, f.kind, a.k, reinterpret_cast<float *>(S.cid), nullptr, nullptr, nullptr, 0};
-    __syncwarp();
-    cnt = greedy_search<CAP, P, CPL, FMT, 1>(ix, key, q, a.ls, a.hbits, S, sink, st);
+    // as the batch path: the plain loop up to h0, the decision outside it
+    // (scratch: the free candidate arrays), the loop re-entered
+    SearchCursor cur{0, 0};
+    int lsq = a.ls, lim = a.pol.mode != JAG_POLICY_PLAIN ? a.pol.h0 : 0x7FFFFFFF;
+    bool decided = false;
+    for (;;) {
+      cnt = greedy_search<CAP, P, CPL, FMT, 0, true>(ix, key, q, lsq, a.hbits, S, sink, st, lim, &cur);
+      if (decided || st.hops < lim) break;
+      __syncwarp();
+      const PolicyOut o = policy_decide(a.pol, S, reinterpret_cast<float *>(S.cid), cnt, a.k, est, f.kind, a.ls,
+                                        nullptr, nullptr);
+      __syncwarp();
+      decided = true;
+      lsq = o.beam;
+      if (cnt > lsq) cnt = lsq;
+      if (o.stop > 0 && st.hops >= o.stop) break;
+      lim = o.stop > 0 ? o.stop : 0x7FFFFFFF;
+      cur.cnt = cnt;
+    }
   } else {
     cnt = greedy_search<CAP, P, CPL, FMT, 0>(ix, key, q, a.ls, a.hbits, S, sink, st);
   }
@@ -285,7 +300,7 @@ serve_kernel(const __grid_constant__ ServeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lcap = list_slots(a.ls);
-  const size_t wbytes = warp_smem_bytes(lcap, a.hbits) + (POL ? kPolicyCtxBytes : 0);
+  const size_t wbytes = warp_smem_bytes(lcap, a.hbits);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, a.hbits);
   for (;;) {

@@ -12,7 +12,7 @@ namespace jag {
 
 template <int P, int CPL, int FMT, bool POL, int CPLF>
 static cudaError_t launch_serve_one(const ServeArgs &a, int ctas, cudaStream_t stream, int *grid_out) {
-  const size_t smem = (size_t)kSearchWarps * (warp_smem_bytes(list_slots(a.ls), a.hbits) + (POL ? kPolicyCtxBytes : 0));
+  const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(list_slots(a.ls), a.hbits);
   auto kern = serve_kernel<256, P, CPL, FMT, POL, CPLF>;
   const int bps = blocks_per_sm(kern, smem);
   if (bps == 0) return cudaErrorInvalidConfiguration;
