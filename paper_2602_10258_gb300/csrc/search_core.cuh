@@ -523,9 +523,12 @@ struct SearchCursor {
 
 // Algorithm 1 for one search by the calling warp.  On return S.bkey/S.bid
 // hold the final list L (count returned).
-// POL: 0 plain search; 1 with the policy's decision at hop h0; 2 as 1, and the
-// trace of the search (decisions and the last hop that changed the first k
-// entries) written to dec_out; the caller fills policy_ctx(S) first.
+// POL: 0 plain search; 1 with the policy's decision at hop h0 taken inside
+// the loop; 2 as 1, and the trace of the search (decisions and the last hop
+// that changed the first k entries) written to dec_out; for 1 and 2 the
+// caller fills policy_ctx(S) first.  The kernels use 2 for traced searches
+// only; an untraced policy search runs POL 0 with RES and takes its decision
+// between two calls (query_kernel, serve_query).
 // RES: the search stops before a hop once st.hops >= max_hops, and ends by
 // storing its cursor in *cur; if cur->cnt > 0 on entry it resumes instead of
 // starting (L, the visited set and st are then as the stopped search left
