@@ -563,6 +563,22 @@ static void policy_features(const entry_t *L, int n, int k, int64_t est, int kin
   f[11] = flog(L[n - 1].dist) * 0.125f;
 }
 
+/* The same features of a list state given entry by entry (first keys,
+ * distances, expanded flags of L[0..n), in the search's order), so that the
+ * tests can pin them on hand-worked lists. */
+void orc_policy_features(const uint32_t *k1, const float *dist, const uint8_t *expanded, int n, int k,
+                         int64_t est, int kind, float *f) {
+  entry_t *L = (entry_t *)malloc(sizeof(entry_t) * (size_t)(n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i) {
+    L[i].k1 = k1[i];
+    L[i].dist = dist[i];
+    L[i].id = i;
+    L[i].expanded = expanded[i] ? 1 : 0;
+  }
+  policy_features(L, n, k, est, kind, f);
+  free(L);
+}
+
 /* Beam and stop hop from the network: the largest beam logit wins (lowest
  * class on a tie); if it leads the runner-up by less than tau the fixed beam
  * is kept and no stop hop is set. */

@@ -86,6 +86,7 @@ def lib():
                 "orc_dist_canon_q_batch": (None, [P, P, P, I32, I64, I64, I64, P]),
                 "orc_query_policy": (I32, [P, P, P, P, I64, I32, I32, I64, I64, P, P, P, P, I32]),
                 "orc_mlp_infer_batch": (None, [P, P, I64, P]),
+                "orc_policy_features": (None, [P, P, P, I32, I32, I64, I32, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -457,6 +458,17 @@ def query_policy(ix: Index, q, filters, aux, k, ls, pol: Policy, s0=0, scan_cap=
     if rc:
         raise ValueError("invalid policy query arguments")
     return ids, dist, cnt
+
+
+def policy_features(k1, dist, expanded, k, est, kind):
+    """The 12 policy features of a list state L given as first keys, fp32
+    distances and expanded flags of its entries in order."""
+    k1 = _c(k1, np.uint32)
+    dist = _c(dist, np.float32)
+    ex = _c(expanded, np.uint8)
+    f = np.zeros(NFEAT, np.float32)
+    lib().orc_policy_features(_p(k1), _p(dist), _p(ex), len(k1), int(k), int(est), int(kind), _p(f))
+    return f
 
 
 def mlp_infer(pol: Policy, X):

@@ -24,9 +24,10 @@
 //            already in L (equal key and id) is dropped;
 // until every entry of L is expanded.
 //
-// The visited set may forget (it is cleared when three quarters full): that
-// only costs recomputation, because an id still in L is caught by the merge
-// (same key, same id) and an id that left L can never re-enter it.
+// The visited set may forget (a new id replaces the first of its two probe
+// slots when both hold other ids): that only costs recomputation, because an
+// id still in L is caught by the merge (same key, same id) and an id that
+// left L can never re-enter it.
 #pragma once
 
 #include "jag_internal.cuh"
