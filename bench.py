@@ -634,9 +634,23 @@ def cpu_baseline(w, idx, beam, gt_ids, gt_d, budget_s=15.0):
         done = sl.stop
     ids = np.concatenate(ids_all)
     rec = recall_at_k(ids, gt_ids[:done], gt_d[:done])
+    check = check_ground_truth(ox, w, gt_ids, gt_d, cores)
     return ({"value": round(done / t_total, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
              "sample": "first %d of the %d queries, beam %d, %.1f s" % (done, len(w.q), beam, t_total),
-             "recall": float(np.nanmean(rec))}, np.concatenate(cnt_all))
+             "recall": float(np.nanmean(rec)), "ground_truth_check": check}, np.concatenate(cnt_all))
+
+
+def check_ground_truth(ox, w, gt_ids, gt_d, cores, n_check=200, seed=5):
+    """The recall ground truth (the GPU's exact scan of every query) against
+    the oracle's brute-force filtered k-NN on a sample of queries (untimed):
+    ids and fp32 distances must be identical, else the run fails."""
+    from oracle import jag_oracle as O
+    sample = np.sort(np.random.default_rng(seed).choice(len(w.q), min(n_check, len(w.q)), replace=False))
+    bi, bd, _, _ = O.brute_force(ox, w.q[sample], w.filters[sample], w.aux, K, nthreads=cores)
+    bad = sample[~((bi == gt_ids[sample]).all(axis=1) & (bd.view(np.uint32) == gt_d[sample].view(np.uint32)).all(axis=1))]
+    if len(bad):
+        raise RuntimeError("ground truth differs from the oracle's brute force on queries %s" % bad[:10].tolist())
+    return {"queries": int(len(sample)), "mismatches": 0, "against": "oracle brute force (exact filtered k-NN)"}
 
 
 def run_reference(args):

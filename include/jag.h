@@ -213,6 +213,16 @@ JAG_API jag_status jag_build(const jag_build_params *params, jag_index **out);
  * JAG_ENOMEM, JAG_ECUDA. */
 JAG_API jag_status jag_search(jag_index *idx, const jag_search_args *args);
 
+/* Query(G, q, l_s, k) of Algorithm 2 as one flat call: the same search as
+ * jag_search with its defaults (s0 = 2048, scan_cap = 8192, default visited
+ * set, no counters, no policy), device pointers queries [nq][d] fp32,
+ * filters [nq], filter_aux (aux_bytes bytes of boolean truth tables, or
+ * NULL), outputs out_ids / out_dist [nq][k]; asynchronous on stream
+ * (cudaStream_t, NULL = legacy default stream).  Errors as jag_search. */
+JAG_API jag_status jag_query(jag_index *idx, const float *queries, const jag_filter *filters,
+                             const uint8_t *filter_aux, int64_t aux_bytes, int64_t nq, int32_t k, int32_t beam,
+                             int32_t *out_ids, float *out_dist, void *stream);
+
 /* Same as jag_search with HOST buffers for queries, filters, aux and
  * outputs: copies them to and from the device inside the call and returns
  * when the answers are in host memory.  args->stream may be NULL. */
@@ -220,24 +230,33 @@ JAG_API jag_status jag_search_host(jag_index *idx, const jag_search_args *args);
 
 /* Search that allocates no device memory.  It does the same work, with the
  * same arguments and answers, as jag_search, but keeps its scratch in a
- * fixed 16 MiB area that the library reserves on every device where it is
- * loaded (held until the process exits), so it never calls cudaMalloc or
+ * fixed 16 MiB area that the library reserves on each device where it builds
+ * an index (held until the process exits), so it never calls cudaMalloc or
  * any other allocating routine.  It serves callers that cannot allocate while
  * they search: a latency-bound serving thread must not wait for the device
  * to drain, as cudaMalloc may; a process may have handed all device memory
  * to its own allocator up front; some deployments forbid allocation after
  * start-up.  The paper has no counterpart; it is a deployment option of this
  * library.
- *   - The first call on a device looks up the area's device address (a
- *     one-time set-up); make that first call before any stream capture.
+ *   - Set-up: jag_build puts the area in place on the index's device and
+ *     looks up its device address; if that failed there, the first call on
+ *     the device does it (then make that first call before any stream
+ *     capture).  With CUDA's lazy module loading the first launch of each of
+ *     the library's kernels in the process loads its code, which the CUDA
+ *     runtime itself may place in device memory: a caller that must not see
+ *     any allocation makes one warm-up call of each kind it will use first.
  *   - Every call, on any stream, uses the same area, which keeps the
  *     previous call's contents; calls whose device work overlaps race, so
  *     issue them on one stream or wait for one before starting the next.
- *   - A call that would need more scratch than 16 MiB (about 32 bytes per
- *     query, 8 bytes per filter_aux byte, and, on indexes with a mask column
- *     and s0 > 0, nq * scan_cap * 4 bytes) returns JAG_EINVAL with the
- *     size it needed in jag_last_error(); split the batch, lower scan_cap,
- *     or set s0 = 0.
+ *   - Scratch a call needs (each region rounded up to 256 bytes): 32 bytes
+ *     per query (plans) + 4 per query (counts) + 8 per filter_aux byte
+ *     (boolean tables) + 512; when s0 > 0: nq * T * (12 * k + 8) bytes
+ *     (partial lists and scan work items, T = ceil(max(s0, scan_cap) / 1024))
+ *     and, on an index with a mask column, nq * scan_cap * 4 (gathered passing
+ *     sets); with JAG_SEARCH_SCAN_ALL: nq * ceil(n / 65536) * 12 * k; on a
+ *     BF16 / FP8 index: nq * min(4k, beam) * 4 (re-ranked ids).  A call that
+ *     would need more than 16 MiB returns JAG_EINVAL with the size it needed
+ *     in jag_last_error(); split the batch, lower scan_cap, or set s0 = 0.
  * Other errors as jag_search. */
 JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_search_args *args);
 

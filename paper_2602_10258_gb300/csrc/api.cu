@@ -144,10 +144,6 @@ void sorted_column(const V *vals, int64_t n, std::vector<V> &sv, std::vector<int
   for (int64_t i = 0; i < n; ++i) { sv[(size_t)i] = tmp[(size_t)i].first; si[(size_t)i] = tmp[(size_t)i].second; }
 }
 
-// 1024 slots (4 KB) at every beam: a larger set costs occupancy, a smaller
-// one recomputation after it is cleared.
-int default_hash_bits(int) { return 10; }
-
 constexpr size_t kSmemLimit = 227 * 1024;
 
 jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
@@ -172,7 +168,7 @@ jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
     }
     if (p->mode == JAG_POLICY_FORCED && !p->forced) return fail(JAG_EINVAL, "forced policy needs `forced`");
   }
-  int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
+  int hb = a->hash_bits ? a->hash_bits : jag::default_hash_bits();
   if (hb < 5 || hb > 16) return fail(JAG_EINVAL, "hash_bits must be in [5, 16]");
   if ((size_t)jag::kSearchWarps * jag::warp_smem_bytes(jag::list_slots(a->beam), hb) > kSmemLimit)
     return fail(JAG_EINVAL, "hash_bits too large for the beam");
@@ -370,6 +366,11 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
   }
   API_TRY(cudaDeviceSynchronize(), "finish upload");
 #undef API_TRY
+  // Put the fixed scratch area of jag_search_noalloc in place on this device
+  // now, while the caller still expects allocations (with lazy module loading
+  // the area would otherwise be loaded by the first no-allocation search).
+  // A failure here is not the build's: that search reports it.
+  if (jag::noalloc_prepare(p->device) != cudaSuccess) cudaGetLastError();
   *out = I;
   return JAG_OK;
 }
@@ -413,19 +414,15 @@ jag_status jag_get_stored_rows(const jag_index *idx, uint8_t *rows_out, float *s
 }
 
 static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream_t stream) {
-  const int hb = a->hash_bits ? a->hash_bits : default_hash_bits(a->beam);
+  const int hb = a->hash_bits ? a->hash_bits : jag::default_hash_bits();
   const int64_t s0 = a->s0 < 0 ? 2048 : a->s0;
   const int64_t cap = a->scan_cap <= 0 ? 8192 : a->scan_cap;
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
-  int32_t ntiles;
-  int64_t tile;
-  const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, cap, a->k, a->beam, idx->n, idx->ix.fmt,
-                                                           scan_all, s0, &ntiles, &tile);
+  const jag::SearchScratch L0 = jag::search_scratch_layout(idx->ix, a->nq, a->aux_bytes, cap, a->k, a->beam, scan_all, s0);
   Workspace *w = idx->workspace(stream);
   std::lock_guard<std::mutex> g(w->mu);
   cudaError_t e = ensure(w->buf, L0.total, stream);
   if (e != cudaSuccess) return cuda_fail(e, "allocate search scratch");
-  uint8_t *base = (uint8_t *)w->buf.ptr;
   jag::SearchLaunch L{};
   L.ix = idx->ix;
   L.queries = a->queries;
@@ -437,17 +434,7 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   L.k = a->k; L.ls = a->beam; L.hbits = hb; L.hbits_auto = a->hash_bits == 0;
   L.s0 = s0; L.cap = cap; L.scan_all = scan_all;
   L.out_ids = a->out_ids; L.out_dist = a->out_dist; L.counters = a->counters;
-  L.plans = (jag::QueryPlan *)(base + L0.plans);
-  L.lut = base + L0.lut;
-  L.lists = (int32_t *)(base + L0.lists);
-  L.list_counts = (int32_t *)(base + L0.list_counts);
-  L.work = (unsigned long long *)(base + L0.work);
-  L.status = (uint32_t *)(base + L0.status);
-  L.part_key = (uint64_t *)(base + L0.part_key);
-  L.part_id = (uint32_t *)(base + L0.part_id);
-  L.ntiles = ntiles; L.tile = tile;
-  L.rr = L0.rr;
-  L.rr_ids = (int32_t *)(base + L0.rr_ids);
+  jag::bind_scratch(L, L0, (uint8_t *)w->buf.ptr);
   if (a->policy) { L.policy = *a->policy; L.has_policy = 1; }
   L.fork_scan = 1;
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
@@ -466,6 +453,24 @@ jag_status jag_search(jag_index *idx, const jag_search_args *a) {
   DeviceGuard dg(idx->device);
   if (!dg.ok) return fail(JAG_ECUDA, "cudaSetDevice failed");
   return search_on(idx, a, (cudaStream_t)a->stream);
+}
+
+jag_status jag_query(jag_index *idx, const float *queries, const jag_filter *filters, const uint8_t *filter_aux,
+                     int64_t aux_bytes, int64_t nq, int32_t k, int32_t beam, int32_t *out_ids, float *out_dist,
+                     void *stream) {
+  jag_search_args a{};
+  a.queries = queries;
+  a.filters = filters;
+  a.filter_aux = filter_aux;
+  a.aux_bytes = aux_bytes;
+  a.nq = nq;
+  a.k = k;
+  a.beam = beam;
+  a.out_ids = out_ids;
+  a.out_dist = out_dist;
+  a.stream = stream;
+  a.s0 = -1;
+  return jag_search(idx, &a);
 }
 
 jag_status jag_search_host(jag_index *idx, const jag_search_args *a) {
@@ -516,12 +521,10 @@ jag_status jag_search_host(jag_index *idx, const jag_search_args *a) {
   uint32_t status = 0;
   Workspace *w = idx->workspace(st);
   if (w->buf.ptr) {
-    int32_t ntiles;
-    int64_t tile;
-    const jag::SearchScratch L0 = jag::search_scratch_layout(a->nq, a->aux_bytes, a->scan_cap <= 0 ? 8192 : a->scan_cap,
-                                                             a->k, a->beam, idx->n, idx->ix.fmt,
+    const jag::SearchScratch L0 = jag::search_scratch_layout(idx->ix, a->nq, a->aux_bytes,
+                                                             a->scan_cap <= 0 ? 8192 : a->scan_cap, a->k, a->beam,
                                                              (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0,
-                                                             a->s0 < 0 ? 2048 : a->s0, &ntiles, &tile);
+                                                             a->s0 < 0 ? 2048 : a->s0);
     if ((e = cudaMemcpyAsync(&status, (uint8_t *)w->buf.ptr + L0.status, 4, cudaMemcpyDeviceToHost, st)))
       return cuda_fail(e, "read status");
   }

@@ -33,6 +33,7 @@ struct SearchLaunch {
   uint32_t *status;
   uint64_t *part_key;      // partial top-k lists [nq][ntiles][k]
   uint32_t *part_id;
+  uint64_t *scan_items;    // [nq * ntiles] (query, tile) work items of the exact scan
   int32_t ntiles;
   int64_t tile;
   jag_policy policy;       // learned / forced beam and stop hop (has_policy)
@@ -48,13 +49,28 @@ struct SearchLaunch {
 template <int FMT>
 cudaError_t launch_graph_fmt(const SearchLaunch &L);
 
-// Scratch layout of a search; sizes in bytes, offsets 256-aligned.
+// Scratch of one search call: byte offsets of its regions (256-aligned) in
+// one buffer, and the total.  A region is sized only when the call can use
+// it: mask lists when the scan route is on and the index has a mask column,
+// partial lists and scan work items when any query can be scanned, re-rank
+// ids for BF16 / FP8 rows.  jag_search, jag_search_host and
+// jag_search_noalloc all lay out their scratch with this one function.
 struct SearchScratch {
-  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, rr_ids, total;
-  int32_t rr;
+  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, scan_items, rr_ids, total;
+  int32_t rr, ntiles;
+  int64_t tile;
 };
-SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int32_t ls, int64_t n,
-                                    int fmt, int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile);
+SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k,
+                                    int32_t ls, int scan_all, int64_t s0);
+// Points the scratch pointers of L into base by the layout s.
+void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base);
+// Default log2 size of the visited set (1024 slots, 4 KB): a larger set costs
+// occupancy, a smaller one recomputation.
+inline int default_hash_bits() { return 10; }
+// Resolves, on the current device, the device address of the fixed scratch
+// area of jag_search_noalloc (noalloc.cu); jag_build calls it so that the
+// area is in place before any search.
+cudaError_t noalloc_prepare(int device);
 // Candidates re-ranked in fp32 per query with BF16 / FP8 rows: min(4k, ls).
 inline int32_t rerank_count(int32_t k, int32_t ls) { return 4 * k < ls ? 4 * k : ls; }
 // Partial top-k lists: the brute-force scan cuts the points into tiles of

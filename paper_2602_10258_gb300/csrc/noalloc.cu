@@ -12,8 +12,11 @@
 //
 // The array (kNoAllocScratchBytes) is part of the library's device image:
 // every GPU on which the library is loaded holds it until the process exits.
-// All calls, on every stream, share it and it keeps the previous call's
-// contents; calls whose device work overlaps therefore race.
+// With CUDA's lazy module loading the array is placed on a device when its
+// address is first looked up; jag_build does that on the index's device, so
+// the area is in place before the first search.  All calls, on every stream,
+// share it and it keeps the previous call's contents; calls whose device
+// work overlaps therefore race.
 #include <cstdio>
 #include <mutex>
 
@@ -32,12 +35,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 uint8_t *g_scratch_ptr[kMaxDevices] = {};
 
-size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
-
-// Device address of the scratch array on the current device.  On the host
-// the array's name is only a stand-in, so the address comes from the
-// runtime, once per device, with that device current.
+// Device address of the scratch array on the current device, which must be
+// `device`.  On the host the array's name is only a stand-in, so the address
+// comes from the runtime, once per device, with that device current.  The
+// lookup also loads the array on that device if it is not loaded yet.
 cudaError_t scratch_address(int device, uint8_t **out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(g_setup_mu);
   if (!g_scratch_ptr[device]) {
     void *p = nullptr;
@@ -50,6 +53,12 @@ cudaError_t scratch_address(int device, uint8_t **out) {
 }
 
 }  // namespace
+
+cudaError_t noalloc_prepare(int device) {
+  uint8_t *p = nullptr;
+  return scratch_address(device, &p);
+}
+
 }  // namespace jag
 
 extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_search_args *a) {
@@ -60,36 +69,20 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   int device = 0;
   index_view(idx, &ix, &device);
   if (device < 0 || device >= kMaxDevices) return set_error(JAG_EUNSUPPORTED, "device ordinal too large");
-  const int64_t nq = a->nq;
   const int64_t s0 = a->s0 < 0 ? 2048 : a->s0;
   const int64_t cap = a->scan_cap <= 0 ? 8192 : a->scan_cap;
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
-  // scratch layout: only the regions this call can touch
-  int64_t tile;
-  int32_t ntiles;
-  scan_tiling(ix.n, scan_all, s0, cap, &ntiles, &tile);
-  const bool lists = !scan_all && s0 > 0 && ix.a_mask != nullptr;
-  size_t off = 0;
-  const size_t o_plans = off; off += a256(sizeof(QueryPlan) * (size_t)(nq > 0 ? nq : 1));
-  const size_t o_lut = off; off += a256((size_t)(a->aux_bytes > 0 ? a->aux_bytes : 1) * 8);
-  const size_t o_lists = off; off += lists ? a256((size_t)nq * (size_t)cap * 4) : 256;
-  const size_t o_counts = off; off += a256(4 * (size_t)(nq > 0 ? nq : 1));
-  const size_t o_work = off; off += 256;
-  const size_t o_status = off; off += 256;
-  const size_t parts = (scan_all || s0 > 0) ? (size_t)nq * (size_t)ntiles * (size_t)a->k : 1;
-  const size_t o_pkey = off; off += a256(parts * 8);
-  const size_t o_pid = off; off += a256(parts * 4);
-  off += (!scan_all && s0 > 0) ? a256(parts * 8) : 0;   // scan work items follow the partial lists
-  const int32_t rr = ix.fmt != JAG_VEC_F32 ? rerank_count(a->k, a->beam) : 0;
-  const size_t o_rr = off; off += a256((size_t)(nq > 0 ? nq : 1) * (size_t)(rr > 0 ? rr : 1) * 4);
-  if (off > kNoAllocScratchBytes) {
+  // the layout jag_search uses, in the fixed area
+  const SearchScratch lay = search_scratch_layout(ix, a->nq, a->aux_bytes, cap, a->k, a->beam, scan_all, s0);
+  if (lay.total > kNoAllocScratchBytes) {
     char msg[256];
     snprintf(msg, sizeof(msg),
              "jag_search_noalloc needs %zu bytes of scratch, more than its fixed %zu; use fewer queries per "
              "call, a smaller scan_cap or filter_aux, s0 = 0, or jag_search",
-             off, kNoAllocScratchBytes);
+             lay.total, kNoAllocScratchBytes);
     return set_error(JAG_EINVAL, msg);
   }
+  if (a->nq == 0) return JAG_OK;
   int prev = 0;
   cudaGetDevice(&prev);
   if (cudaSetDevice(device) != cudaSuccess) return set_error(JAG_ECUDA, "cudaSetDevice failed");
@@ -99,7 +92,6 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
     cudaSetDevice(prev);
     return set_error(JAG_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed");
   }
-  cudaStream_t stream = (cudaStream_t)a->stream;
   SearchLaunch L{};
   L.ix = ix;
   L.queries = a->queries;
@@ -107,29 +99,19 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   L.filters = a->filters;
   L.aux = a->filter_aux;
   L.aux_bytes = a->aux_bytes;
-  L.nq = nq;
+  L.nq = a->nq;
   L.k = a->k; L.ls = a->beam;
-  L.hbits = a->hash_bits ? a->hash_bits : 10;
+  L.hbits = a->hash_bits ? a->hash_bits : default_hash_bits();
   L.hbits_auto = a->hash_bits == 0;
   L.s0 = s0; L.cap = cap; L.scan_all = scan_all;
   L.out_ids = a->out_ids; L.out_dist = a->out_dist; L.counters = a->counters;
-  L.plans = (QueryPlan *)(base + o_plans);
-  L.lut = base + o_lut;
-  L.lists = (int32_t *)(base + o_lists);
-  L.list_counts = (int32_t *)(base + o_counts);
-  L.work = (unsigned long long *)(base + o_work);
-  L.status = (uint32_t *)(base + o_status);
-  L.part_key = (uint64_t *)(base + o_pkey);
-  L.part_id = (uint32_t *)(base + o_pid);
-  L.ntiles = ntiles; L.tile = tile;
-  L.rr = rr;
-  L.rr_ids = (int32_t *)(base + o_rr);
+  bind_scratch(L, lay, base);
   if (a->policy) { L.policy = *a->policy; L.has_policy = 1; }
   L.ev_begin = (cudaEvent_t)a->ev_graph_begin;
   L.ev_end = (cudaEvent_t)a->ev_graph_end;
-  L.stream = stream;
+  L.stream = (cudaStream_t)a->stream;
   // the status word must start at zero (the work counters are cleared by the launch sequence)
-  e = cudaMemsetAsync(L.status, 0, 4, stream);
+  e = cudaMemsetAsync(L.status, 0, 4, L.stream);
   if (e == cudaSuccess) e = run_search(L);
   cudaSetDevice(prev);
   if (e != cudaSuccess) return set_error(JAG_ECUDA, cudaGetErrorString(e));

@@ -508,25 +508,44 @@ int scan_rows_per_round(int64_t xs) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(32, r));
 }
 
-SearchScratch search_scratch_layout(int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k, int32_t ls, int64_t n,
-                                    int fmt, int scan_all, int64_t s0, int32_t *ntiles, int64_t *tile) {
+SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k,
+                                    int32_t ls, int scan_all, int64_t s0) {
   SearchScratch s;
+  const size_t q1 = (size_t)std::max<int64_t>(nq, 1);
+  scan_tiling(ix.n, scan_all, s0, cap, &s.ntiles, &s.tile);
+  const bool lists = !scan_all && s0 > 0 && ix.a_mask != nullptr;
+  const bool scans = scan_all || s0 > 0;
   size_t off = 0;
-  s.plans = off; off += align256(sizeof(QueryPlan) * (size_t)std::max<int64_t>(nq, 1));
+  s.plans = off; off += align256(sizeof(QueryPlan) * q1);
   s.lut = off; off += align256((size_t)std::max<int64_t>(aux_bytes, 1) * 8);
-  s.lists = off; off += scan_all ? 256 : align256((size_t)std::max<int64_t>(nq, 1) * (size_t)cap * 4);
-  s.list_counts = off; off += align256((size_t)std::max<int64_t>(nq, 1) * 4);
+  s.lists = off; off += lists ? align256(q1 * (size_t)cap * 4) : 256;
+  s.list_counts = off; off += align256(q1 * 4);
   s.work = off; off += 256;
   s.status = off; off += 256;
-  scan_tiling(n, scan_all, s0, cap, ntiles, tile);
-  const size_t parts = (scan_all || s0 > 0) ? (size_t)std::max<int64_t>(nq, 1) * *ntiles * k : 1;
+  const size_t parts = scans ? q1 * (size_t)s.ntiles * (size_t)k : 1;
   s.part_key = off; off += align256(parts * 8);
   s.part_id = off; off += align256(parts * 4);
-  off += (!scan_all && s0 > 0) ? align256(parts * 8) : 0;   // scan work items, right after part_id
-  s.rr = fmt != JAG_VEC_F32 ? rerank_count(k, ls) : 0;
-  s.rr_ids = off; off += align256((size_t)std::max<int64_t>(nq, 1) * std::max(s.rr, 1) * 4);
+  s.scan_items = off; off += (!scan_all && s0 > 0) ? align256(q1 * (size_t)s.ntiles * 8) : 256;
+  s.rr = ix.fmt != JAG_VEC_F32 ? rerank_count(k, ls) : 0;
+  s.rr_ids = off; off += align256(q1 * (size_t)std::max(s.rr, 1) * 4);
   s.total = off;
   return s;
+}
+
+void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base) {
+  L.plans = reinterpret_cast<QueryPlan *>(base + s.plans);
+  L.lut = base + s.lut;
+  L.lists = reinterpret_cast<int32_t *>(base + s.lists);
+  L.list_counts = reinterpret_cast<int32_t *>(base + s.list_counts);
+  L.work = reinterpret_cast<unsigned long long *>(base + s.work);
+  L.status = reinterpret_cast<uint32_t *>(base + s.status);
+  L.part_key = reinterpret_cast<uint64_t *>(base + s.part_key);
+  L.part_id = reinterpret_cast<uint32_t *>(base + s.part_id);
+  L.scan_items = reinterpret_cast<uint64_t *>(base + s.scan_items);
+  L.ntiles = s.ntiles;
+  L.tile = s.tile;
+  L.rr = s.rr;
+  L.rr_ids = reinterpret_cast<int32_t *>(base + s.rr_ids);
 }
 
 template <int CAP, int P, int CPL>
@@ -536,9 +555,8 @@ static cudaError_t launch_scan(const SearchLaunch &L) {
   const int rpr = scan_rows_per_round(L.ix.xs);
   const size_t ssm = (size_t)kScanWarps * (warp_smem_bytes(list_slots(L.k), 5) + 32 * 4 + 2 * (size_t)rpr * L.ix.xs * 4);
   auto sk = scan_tile_kernel<CAP, P, CPL>;
-  // items live after the partial lists' id array; counters in work[2..3]
-  uint64_t *items = reinterpret_cast<uint64_t *>(L.part_id + (size_t)std::max<int64_t>(L.nq, 1) * L.ntiles * L.k);
-  items = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(items) + 255) & ~uintptr_t(255));
+  // work items in their own scratch region; counters in work[2..3]
+  uint64_t *items = L.scan_items;
   scan_items_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.ix, L.filters, L.plans, L.lists, L.cap,
                                                                           L.nq, L.tile, items, L.work + 3);
   const int sbps = blocks_per_sm(sk, ssm, kScanWarps);

@@ -81,7 +81,7 @@ class Info(C.Structure):
                 ("reserved", C.c_int32)]
 
 
-EXPORTED = ["jag_build", "jag_search", "jag_search_host", "jag_search_noalloc", "jag_get_info",
+EXPORTED = ["jag_build", "jag_search", "jag_query", "jag_search_host", "jag_search_noalloc", "jag_get_info",
             "jag_get_graph", "jag_get_thresholds", "jag_get_stored_rows", "jag_free", "jag_last_error",
             "jag_version", "jag_mlp_loss_grad", "jag_mlp_train", "jag_mlp_export", "jag_serve_start",
             "jag_serve_submit", "jag_serve_wait", "jag_serve_replay", "jag_serve_info", "jag_serve_stop"]
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
             L.jag_build.restype = C.c_int
             L.jag_search.argtypes = [P, C.POINTER(SearchArgs)]
             L.jag_search.restype = C.c_int
+            L.jag_query.argtypes = [P, P, P, P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, P, P, P]
+            L.jag_query.restype = C.c_int
             L.jag_search_host.argtypes = [P, C.POINTER(SearchArgs)]
             L.jag_search_host.restype = C.c_int
             L.jag_search_noalloc.argtypes = [P, C.POINTER(SearchArgs)]
@@ -266,6 +268,17 @@ def jag_search(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=No
     ps = None if policy is None else policy.struct()
     a.policy = None if ps is None else C.addressof(ps)
     _check(L.jag_search(h, C.byref(a)))
+
+
+def jag_query(h, queries, filters, aux, k, beam, out_ids, out_dist, stream=None):
+    """The flat Query call (Algorithm 2) with the library's defaults: CUDA
+    tensors as in jag_search; asynchronous on ``stream``."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(queries.device)
+    nb = 0 if aux is None else aux.numel()
+    _check(load().jag_query(h, queries.data_ptr(), filters.data_ptr(), None if nb == 0 else aux.data_ptr(), nb,
+                            queries.shape[0], int(k), int(beam), out_ids.data_ptr(), out_dist.data_ptr(),
+                            st.cuda_stream))
 
 
 def jag_search_noalloc(h, queries, filters, aux, k, beam, out_ids, out_dist, counters=None, stream=None,

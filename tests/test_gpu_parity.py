@@ -318,3 +318,18 @@ def test_concurrent_streams_same_answers(range_small):
             out.append(gi.search(q, w.filters, w.aux, 10, 64, stream=s))
     torch.cuda.synchronize()
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_flat_query_call(label_case):
+    """jag_query (the flat Query(G, q, l_s, k) call with the library defaults)
+    answers as jag_search with s0 = 2048 and as the oracle."""
+    w, ix, _, gi = label_case
+    q = torch.from_numpy(w.q).cuda()
+    ft = jag.filters_to_device(w.filters, q.device)
+    at = jag.aux_to_device(w.aux, q.device)
+    ids = torch.empty((len(w.q), 10), dtype=torch.int32, device=q.device)
+    dist = torch.empty((len(w.q), 10), dtype=torch.float32, device=q.device)
+    jag.jag_query(gi.h, q, ft, at, 10, 48, ids, dist)
+    torch.cuda.synchronize()
+    rid, rd, rc = O.query(ix, w.q, w.filters, w.aux, 10, 48, s0=2048, scan_cap=8192)
+    assert_parity(ids.cpu().numpy(), dist.cpu().numpy(), rid, rd, "jag_query")
