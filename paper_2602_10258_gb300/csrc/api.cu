@@ -273,6 +273,14 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
   API_TRY(cudaMemcpy2D(I->x, sizeof(float) * xs, p->x, sizeof(float) * d, sizeof(float) * d, (size_t)n,
                        cudaMemcpyHostToDevice), "copy vectors");
   ix.x = I->x;
+  {
+    float *xn;
+    unsigned int *dmax;
+    API_TRY(I->alloc((void **)&xn, sizeof(float) * (size_t)n), "allocate row norms");
+    API_TRY(I->alloc((void **)&dmax, sizeof(unsigned int)), "allocate row norms");
+    API_TRY(jag::row_norms(ix, xn, dmax, &ix.xnorm_max, 0), "row norms");
+    ix.xnorm = xn;
+  }
   ix.fmt = p->storage;
   if (p->storage != JAG_VEC_F32) {
     const int64_t eb = p->storage == JAG_VEC_BF16 ? 2 : 1;
@@ -418,7 +426,7 @@ static jag_status search_on(jag_index *idx, const jag_search_args *a, cudaStream
   const int64_t s0 = a->s0 < 0 ? 2048 : a->s0;
   const int64_t cap = a->scan_cap <= 0 ? 8192 : a->scan_cap;
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
-  const jag::SearchScratch L0 = jag::search_scratch_layout(idx->ix, a->nq, a->aux_bytes, cap, a->k, a->beam, scan_all, s0);
+  const jag::SearchScratch L0 = jag::search_scratch_layout(idx->ix, a->nq, a->aux_bytes, cap, a->k, a->beam, scan_all, s0, 1);
   Workspace *w = idx->workspace(stream);
   std::lock_guard<std::mutex> g(w->mu);
   cudaError_t e = ensure(w->buf, L0.total, stream);
@@ -524,11 +532,12 @@ jag_status jag_search_host(jag_index *idx, const jag_search_args *a) {
     const jag::SearchScratch L0 = jag::search_scratch_layout(idx->ix, a->nq, a->aux_bytes,
                                                              a->scan_cap <= 0 ? 8192 : a->scan_cap, a->k, a->beam,
                                                              (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0,
-                                                             a->s0 < 0 ? 2048 : a->s0);
+                                                             a->s0 < 0 ? 2048 : a->s0, 1);
     if ((e = cudaMemcpyAsync(&status, (uint8_t *)w->buf.ptr + L0.status, 4, cudaMemcpyDeviceToHost, st)))
       return cuda_fail(e, "read status");
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "search");
+  if (status & jag::kErrTcTimeout) return fail(JAG_ETIMEOUT, "the exact scan's tensor-core wait timed out");
   if (status & jag::kErrBadFilter) return fail(JAG_EINVAL, "invalid filter record(s): their answers are padded");
   return JAG_OK;
 }

@@ -64,6 +64,11 @@ struct DevIndex {
   int32_t qbytes;           // bytes per stored row (multiple of 16)
   int32_t qchunks;          // 16-byte chunks per stored row
   int32_t pad1;
+  // |x|^2 of every fp32 row (any summation order) and the largest of them:
+  // the exact scan's approximate distances and their error bound
+  const float *xnorm;
+  float xnorm_max;
+  int32_t pad2;
 };
 
 // Elements of one 16-byte chunk of a stored row, per format.
@@ -321,6 +326,8 @@ enum : uint32_t {
   kErrVisitedOverflow = 1u,
   kErrCandOverflow = 2u,
   kErrBadFilter = 4u,
+  kErrTcTimeout = 16u,   // the tensor-core scan gave up waiting for its MMAs
+  kErrTcBound = 32u,     // a scan candidate broke the approximation bound (its query was rescanned exactly)
 };
 
 }  // namespace jag

@@ -8,6 +8,17 @@
 
 namespace jag {
 
+// Scratch of the tensor-core exact scan (scan_tc.cu): approximate distances
+// [nq][cap], the grouping hash table (slots entries) and the group members.
+struct TcScratch {
+  float *approx;
+  uint64_t *hkey;
+  int32_t *hcnt, *hrep, *hoff, *gl;
+  int64_t *ioff;
+  int32_t *gslot, *gmem, *members;
+  size_t slots;
+};
+
 // One jag_search call, resolved to device pointers.
 struct SearchLaunch {
   DevIndex ix;
@@ -43,6 +54,7 @@ struct SearchLaunch {
   cudaEvent_t ev_begin, ev_end;
   cudaStream_t stream;
   int32_t fork_scan;       // run the exact scan on a side stream, concurrently
+  TcScratch tc;            // tensor-core scan scratch; tc.approx == nullptr: the fp32 scan kernels
 };
 
 // Graph-search launch for rows stored in format FMT (search_<fmt>.cu).
@@ -55,13 +67,17 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L);
 // partial lists and scan work items when any query can be scanned, re-rank
 // ids for BF16 / FP8 rows.  jag_search, jag_search_host and
 // jag_search_noalloc all lay out their scratch with this one function.
+// With tc, the scan route runs on the tensor cores (scan_tc.cu) and its
+// regions replace the fp32 scan's partial lists and work items.
 struct SearchScratch {
-  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, scan_items, rr_ids, total;
-  int32_t rr, ntiles;
+  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, scan_items, rr_ids;
+  size_t approx, hkey, hcnt, hrep, hoff, gl, ioff, gslot, gmem, members, slots;
+  size_t total;
+  int32_t rr, ntiles, tc;
   int64_t tile;
 };
 SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k,
-                                    int32_t ls, int scan_all, int64_t s0);
+                                    int32_t ls, int scan_all, int64_t s0, int tc);
 // Points the scratch pointers of L into base by the layout s.
 void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base);
 // Default log2 size of the visited set (1024 slots, 4 KB): a larger set costs
@@ -79,6 +95,14 @@ inline int32_t rerank_count(int32_t k, int32_t ls) { return 4 * k < ls ? 4 * k :
 void scan_tiling(int64_t n, int scan_all, int64_t s0, int64_t cap, int32_t *ntiles, int64_t *tile);
 
 cudaError_t run_search(const SearchLaunch &L);
+
+// The tensor-core exact scan of the scan-routed queries (scan_tc.cu).
+cudaError_t launch_scan_tc(const SearchLaunch &L);
+// Hash-table slots of the scan's grouping for nq queries: a power of two >= 2 nq.
+size_t tc_table_slots(int64_t nq);
+// |x|^2 of every row into xn and their maximum into *xmax_host (dmax: one
+// device word of scratch); synchronous on stream.
+cudaError_t row_norms(const DevIndex &ix, float *xn, unsigned int *dmax, float *xmax_host, cudaStream_t stream);
 
 // Smallest supported list capacity >= ls (64, 128 or 256); 0 if ls > 256.
 int list_capacity(int ls);

@@ -73,7 +73,9 @@ extern "C" JAG_API jag_status jag_search_noalloc(jag_index *idx, const jag_searc
   const int64_t cap = a->scan_cap <= 0 ? 8192 : a->scan_cap;
   const int scan_all = (a->flags & JAG_SEARCH_SCAN_ALL) ? 1 : 0;
   // the layout jag_search uses, in the fixed area
-  const SearchScratch lay = search_scratch_layout(ix, a->nq, a->aux_bytes, cap, a->k, a->beam, scan_all, s0);
+  // (with the fp32 scan kernels, whose scratch is far smaller than the
+  // tensor-core scan's nq * scan_cap approximations; the answers are the same)
+  const SearchScratch lay = search_scratch_layout(ix, a->nq, a->aux_bytes, cap, a->k, a->beam, scan_all, s0, 0);
   if (lay.total > kNoAllocScratchBytes) {
     char msg[256];
     snprintf(msg, sizeof(msg),

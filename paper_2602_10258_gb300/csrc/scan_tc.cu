@@ -1,0 +1,581 @@
+// Exact pre-filter scan on the tensor cores (the Pre-Filtering baseline of
+// the experiments, for the queries routed to the scan).
+//
+// Queries whose passing sets are the same slice of a sorted column (every
+// query of one label, say) share their rows, so a group's distances form one
+// dense contraction: rows x queries over the dimension.  The scan runs in
+// three steps:
+//
+//  1. grouping   scan-routed queries are grouped by passing set (the slice's
+//                bounds; a gathered subset / boolean list is a group of its
+//                own) with a hash table in device memory;
+//  2. contract   a CTA takes 128 rows of a group and up to 64 of its queries,
+//                gathers the fp32 rows and queries into shared memory in the
+//                tensor core's K-major layout, and computes all dot products
+//                with tcgen05.mma (kind::tf32, accumulators in tensor
+//                memory); the epilogue writes the approximate squared
+//                distance a = |x|^2 + |q|^2 - 2 q.x of every (query, row);
+//  3. select     one warp per query finds a threshold tau that at least k
+//                rows reach (the k-th smallest of a sample of the a values),
+//                computes the canonical fp32 distance of every row with
+//                a <= tau + 2 eps, and keeps the best k by (distance, id).
+//
+// eps bounds |a - d| for the canonical fp32 distance d of any row:
+//   eps = (2^-8 + dim 2^-20) (|q|^2 + max_x |x|^2) + 2^-100.
+// TF32 operands carry 10 fraction bits (relative error < 2^-10 each, so a
+// product is within 2^-8.99 of q_i x_i); the fp32 accumulation of dim + 8
+// terms adds at most (dim + 8) 2^-22 of sum |q_i x_i| even if every addition
+// is off by two units in the last place; |x|^2, |q|^2, the canonical
+// distance and the final two operations add (3 dim + 8) 2^-24 of
+// (|q|^2 + |x|^2); and sum |q_i x_i| <= (|q|^2 + |x|^2) / 2.  The bound is
+// twice that sum.  Any row among the exact top k then has a <= tau + 2 eps:
+// at least k rows have d <= tau + eps, so the k-th distance is at most
+// tau + eps.  The answers are therefore the exact top k whatever the
+// approximation, provided the bound holds; the select step checks it on
+// every candidate and, should it ever fail, takes every row as a candidate.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "launch.h"
+#include "launch_util.cuh"
+#include "search_core.cuh"
+
+namespace jag {
+
+namespace {
+
+constexpr int kTcRows = 128;         // rows per tile: the MMA's M
+constexpr int kTcQueries = 64;       // queries per tile at most: the MMA's N (padded to 16)
+constexpr int kTcK = 128;            // fp32 elements of a row per pass (K chunk)
+constexpr int kTcThreads = 128;      // four warps: one per 32-lane quarter of tensor memory
+constexpr int kTcCols = 64;          // tensor-memory columns allocated (>= kTcQueries, a power of two >= 32)
+constexpr uint32_t kTcSbo = kTcK * 32;                       // bytes between 8-row groups of an operand
+constexpr size_t kTcSmemA = (size_t)kTcRows * kTcK * 4;      // 64 KB
+constexpr size_t kTcSmemB = (size_t)kTcQueries * kTcK * 4;   // 32 KB
+constexpr size_t kTcSmem = kTcSmemA + kTcSmemB + 1024;      // + alignment slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling:
+// 8-row x 16-byte core matrices, adjacent along K at lbo bytes, 8-row groups
+// at sbo bytes; version bits 46-48 = 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: fp32 accumulator (bits 4-5 = 1), A and
+// B in TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at
+// bit 24.
+__device__ __forceinline__ uint32_t tf32_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Bounded wait for the phase `parity` of an mbarrier (about a second at
+// most); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it >= 16) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t v) {
+  v ^= v >> 33; v *= 0xFF51AFD7ED558CCDull; v ^= v >> 33; v *= 0xC4CEB9FE1A85EC53ull; v ^= v >> 33;
+  return v;
+}
+
+// The group key of a scan-routed query: its slice (column, begin, end), or,
+// for a gathered list, the query itself.
+__device__ __forceinline__ uint64_t group_key(const QueryPlan &pl, int32_t kind, int64_t qi) {
+  if (pl.route == kRouteSlice)
+    return ((uint64_t)(kind == JAG_F_RANGE_F32 ? 1 : 0) << 62) | ((uint64_t)pl.begin << 31) | (uint64_t)pl.end;
+  return (1ull << 63) | (uint64_t)qi;
+}
+
+__device__ __forceinline__ bool scan_routed(int32_t route) { return route == kRouteSlice || route == kRouteList; }
+
+__device__ __forceinline__ void group_rows(const DevIndex &ix, const jag_filter *filters, const QueryPlan &pl,
+                                           int64_t qi, const int32_t *lists, int64_t cap, const int32_t **ids,
+                                           int64_t *m) {
+  if (pl.route == kRouteSlice) {
+    *ids = (filters[qi].kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
+    *m = pl.end - pl.begin;
+  } else {
+    *ids = lists + qi * cap;
+    *m = pl.count;
+  }
+}
+
+// (1a) every scan-routed query joins the group of its key.
+__global__ void tc_group_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, uint64_t *hkey,
+                                int32_t *hcnt, int32_t *hrep, uint32_t hmask, int32_t *gslot, int32_t *gmem) {
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= nq) return;
+  const QueryPlan pl = plans[qi];
+  if (!scan_routed(pl.route)) { gslot[qi] = -1; return; }
+  const uint64_t key = group_key(pl, filters[qi].kind, qi);
+  uint32_t h = (uint32_t)mix64(key) & hmask;
+  for (uint32_t probe = 0; probe <= hmask; ++probe) {   // the table has at least 2 nq slots
+    const unsigned long long old = atomicCAS((unsigned long long *)&hkey[h], ~0ull, (unsigned long long)key);
+    if (old == ~0ull || old == key) break;
+    h = (h + 1) & hmask;
+  }
+  const int32_t j = atomicAdd(&hcnt[h], 1);
+  if (j == 0) hrep[h] = (int32_t)qi;
+  gslot[qi] = (int32_t)h;
+  gmem[qi] = j;
+}
+
+// Inclusive block-wide sum of v over kTcLayoutThreads threads.
+constexpr int kTcLayoutThreads = 1024;
+__device__ __forceinline__ int64_t block_scan_incl(int64_t v, int64_t *wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += t;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  const int64_t r = v + (warp > 0 ? wsum[warp - 1] : 0);
+  __syncthreads();
+  return r;
+}
+
+// (1b) one CTA numbers the groups (slot order), places their members
+// (hoff: first member position) and counts their work items: one per
+// (128-row tile, chunk of up to 64 queries); gl[g] = slot of group g,
+// ioff[g] = first item of group g; counters[0] = groups, counters[1] = items.
+__global__ void __launch_bounds__(kTcLayoutThreads)
+tc_layout_kernel(DevIndex ix, const jag_filter *filters, const QueryPlan *plans, const int32_t *lists, int64_t cap,
+                 const int32_t *hcnt, const int32_t *hrep, int64_t H, int32_t *hoff, int32_t *gl, int64_t *ioff,
+                 unsigned long long *counters) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t tot[3];
+  int64_t ng = 0, nm = 0, ni = 0;
+  for (int64_t base = 0; base < H; base += kTcLayoutThreads) {
+    const int64_t s = base + threadIdx.x;
+    const int32_t c = s < H ? hcnt[s] : 0;
+    int64_t items = 0;
+    if (c > 0) {
+      const int32_t r = hrep[s];
+      const int32_t *ids;
+      int64_t m;
+      group_rows(ix, filters, plans[r], r, lists, cap, &ids, &m);
+      items = ((m + kTcRows - 1) / kTcRows) * ((c + kTcQueries - 1) / kTcQueries);
+    }
+    const int64_t g_incl = block_scan_incl(c > 0 ? 1 : 0, wsum);
+    const int64_t m_incl = block_scan_incl(c, wsum);
+    const int64_t i_incl = block_scan_incl(items, wsum);
+    if (c > 0) {
+      const int64_t g = ng + g_incl - 1;
+      gl[g] = (int32_t)s;
+      hoff[s] = (int32_t)(nm + m_incl - c);
+      ioff[g] = ni + i_incl - items;
+    }
+    // totals of this round: the last thread's inclusive sums
+    if (threadIdx.x == kTcLayoutThreads - 1) { tot[0] = g_incl; tot[1] = m_incl; tot[2] = i_incl; }
+    __syncthreads();
+    ng += tot[0]; nm += tot[1]; ni += tot[2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { counters[0] = (unsigned long long)ng; counters[1] = (unsigned long long)ni; }
+}
+
+// (1c) members of each group in consecutive positions.
+__global__ void tc_member_kernel(int64_t nq, const int32_t *gslot, const int32_t *gmem, const int32_t *hoff,
+                                 int32_t *members) {
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= nq) return;
+  const int32_t s = gslot[qi];
+  if (s >= 0) members[hoff[s] + gmem[qi]] = (int32_t)qi;
+}
+
+// (2) the contraction.  Persistent CTAs of four warps claim work items; per
+// item: the rows and queries go to shared memory (rows by 16-byte cp.async
+// from the fp32 rows, queries by plain loads, both zero padded), one thread
+// issues the MMAs of each 128-element K chunk into tensor memory, and after
+// the MMAs' commit the four warps read their 32 rows each and write the
+// approximate distances approx[q][position of the row in q's passing set].
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
+                   const int32_t *lists, int64_t cap, const int32_t *hcnt, const int32_t *hrep, const int32_t *hoff,
+                   const int32_t *gl, const int64_t *ioff, const int32_t *members, unsigned long long *counters,
+                   float *approx, uint32_t *status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float *sa = reinterpret_cast<float *>(smem);
+  float *sb = reinterpret_cast<float *>(smem + kTcSmemA);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_taddr;
+  __shared__ int64_t s_item;
+  __shared__ int32_t s_qid[kTcQueries];
+  __shared__ float s_qn[kTcQueries];
+  __shared__ int32_t s_rid[kTcRows];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t mbar_addr = smem_u32(&mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_addr) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_taddr;
+  const uint32_t sa_addr = smem_u32(sa), sb_addr = smem_u32(sb);
+  const unsigned long long ng = counters[0], ni = counters[1];
+  uint32_t phase = 0;
+  const int nkc = (d + kTcK - 1) / kTcK;
+  for (;;) {
+    if (tid == 0) s_item = (int64_t)atomicAdd(counters + 2, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();   // every thread has read s_item before the next claim overwrites it
+    if (item >= (int64_t)ni) break;
+    // the item's group: the last g with ioff[g] <= item
+    int64_t lo = 0, hi = (int64_t)ng - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (ioff[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int32_t slot = gl[lo];
+    const int32_t nmem = hcnt[slot];
+    const int32_t rep = hrep[slot];
+    const int32_t *ids;
+    int64_t m;
+    group_rows(ix, filters, plans[rep], rep, lists, cap, &ids, &m);
+    const int64_t nchunk = (nmem + kTcQueries - 1) / kTcQueries;
+    const int64_t local = item - ioff[lo];
+    const int64_t tile = local / nchunk, chunk = local % nchunk;
+    const int64_t r0 = tile * kTcRows;
+    const int nrow = (int)min64(kTcRows, m - r0);
+    const int nqc = (int)min64(kTcQueries, (int64_t)nmem - chunk * kTcQueries);
+    const int N = (nqc + 15) & ~15;
+    if (tid < kTcQueries) s_qid[tid] = tid < nqc ? members[hoff[slot] + chunk * kTcQueries + tid] : -1;
+    s_rid[tid] = tid < nrow ? ids[r0 + tid] : -1;
+    __syncthreads();
+    // |q|^2 of the chunk's queries, one warp per query
+    for (int j = warp; j < nqc; j += kTcThreads / 32) {
+      const float *qr = queries + (int64_t)s_qid[j] * d;
+      float acc = 0.f;
+      for (int e = lane; e < d; e += 32) acc = __fmaf_rn(qr[e], qr[e], acc);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(kFull, acc, o));
+      if (lane == 0) s_qn[j] = acc;
+    }
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int k0 = kc * kTcK;
+      const int kw = min(kTcK, ((d - k0) + 7) & ~7);   // elements of this chunk, a multiple of 8
+      const int c4n = kw / 4;                          // 16-byte chunks per row
+      // rows: lane -> (row % 8, chunk), so a warp writes 8 rows x 4 chunks of 16 bytes
+      for (int blk = warp; blk < (kTcRows / 8) * ((c4n + 3) / 4); blk += kTcThreads / 32) {
+        const int rg = blk % (kTcRows / 8), cg = blk / (kTcRows / 8);
+        const int r = rg * 8 + (lane & 7), c4 = cg * 4 + (lane >> 3);
+        if (c4 < c4n) {
+          const int kk = k0 + 4 * c4;
+          const int32_t id = s_rid[r];
+          const bool ok = id >= 0 && kk < ix.xs;
+          const float *src = ok ? ix.x + (int64_t)id * ix.xs + kk : ix.x;
+          cp_async16(sa_addr + rg * kTcSbo + c4 * 128 + (r & 7) * 16, src, ok ? 16u : 0u);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      // queries: plain loads (rows of d floats need not be 16-byte aligned)
+      for (int e = tid; e < N * c4n; e += kTcThreads) {
+        const int n = e / c4n, c4 = e - n * c4n;
+        const int kk = k0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < nqc) {
+          const float *qr = queries + (int64_t)s_qid[n] * d;
+          v.x = kk + 0 < d ? qr[kk + 0] : 0.f;
+          v.y = kk + 1 < d ? qr[kk + 1] : 0.f;
+          v.z = kk + 2 < d ? qr[kk + 2] : 0.f;
+          v.w = kk + 3 < d ? qr[kk + 3] : 0.f;
+        }
+        *reinterpret_cast<float4 *>(reinterpret_cast<uint8_t *>(sb) + (n >> 3) * kTcSbo + c4 * 128 + (n & 7) * 16) = v;
+      }
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint32_t idesc = tf32_idesc(kTcRows, N);
+        for (int s = 0; s < kw / 8; ++s) {
+          const uint64_t ad = smem_desc(sa_addr + s * 256, 128, kTcSbo);
+          const uint64_t bd = smem_desc(sb_addr + s * 256, 128, kTcSbo);
+          const uint32_t accum = (kc > 0 || s > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
+                     : "memory");
+      }
+      const bool ok = __syncthreads_and(mbar_wait(mbar_addr, phase) ? 1 : 0) != 0;
+      phase ^= 1u;
+      tc_fence_after();
+      if (!ok) {
+        // the MMAs did not complete in time: give them a second bounded wait
+        // before tensor memory is released, flag the error and stop
+        if (tid == 0) { atomicOr(status, kErrTcTimeout); s_abort = 1; }
+        mbar_wait(mbar_addr, phase ^ 1u);
+        break;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // epilogue: warp w holds rows 32w + lane in tensor-memory lanes 32w..32w+31
+    const int r = warp * 32 + lane;
+    const int32_t rid = s_rid[r];
+    const float xn = rid >= 0 ? ix.xnorm[rid] : 0.f;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = c0 + j;
+        if (n < nqc && r < nrow) {
+          const float a = __fsub_rn(__fadd_rn(xn, s_qn[n]), __fmul_rn(2.f, u2f(v[j])));
+          approx[(int64_t)s_qid[n] * cap + r0 + r] = a;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();   // shared memory and tensor memory are reused by the next item
+    tc_fence_after();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+}
+
+// (3) selection per scan-routed query (one warp each), see the file comment.
+template <int CAP, int P, int CPL>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+tc_select_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
+                 const int32_t *lists, int64_t cap, int64_t nq, int k, const float *approx, int32_t *out_ids,
+                 float *out_dist, int32_t *counters, uint32_t *status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lcap = list_slots(k);
+  const WarpSmem S = carve_warp_smem(smem + warp * warp_smem_bytes(lcap, 5), lcap, 5);
+  const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + warp;
+  if (qi >= nq) return;
+  const QueryPlan pl = plans[qi];
+  if (!scan_routed(pl.route)) return;
+  const int32_t *ids;
+  int64_t m;
+  group_rows(ix, filters, pl, qi, lists, cap, &ids, &m);
+  const float *a = approx + qi * cap;
+  QChunks<CPL, JAG_VEC_F32> q;
+  load_point<P, CPL>(queries + qi * d, d, q);
+  // eps from |q|^2 and the largest |x|^2 of the index
+  float qn = 0.f;
+  for (int e = lane; e < d; e += 32) { const float t = queries[qi * d + e]; qn = __fmaf_rn(t, t, qn); }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) qn = __fadd_rn(qn, __shfl_xor_sync(kFull, qn, o));
+  const float eps = __fmaf_rn(__fadd_rn(0.00390625f, __fmul_rn((float)d, 9.5367431640625e-07f)),
+                              __fadd_rn(qn, ix.xnorm_max), 7.888609052210118e-31f);
+  // tau: the k-th smallest of the four smallest a values of every lane (at
+  // least k rows have a <= tau); every row is a candidate when m <= 4k or k > 128
+  float thr = INFINITY;
+  if (m > 4 * (int64_t)k && k <= 128) {
+    float r0 = INFINITY, r1 = INFINITY, r2 = INFINITY, r3 = INFINITY;
+    for (int64_t j = lane; j < m; j += 32) {
+      float v = a[j];
+      if (v < r3) {
+        r3 = v;
+        if (r3 < r2) { const float t = r2; r2 = r3; r3 = t; }
+        if (r2 < r1) { const float t = r1; r1 = r2; r2 = t; }
+        if (r1 < r0) { const float t = r0; r0 = r1; r1 = t; }
+      }
+    }
+    float tau = INFINITY;
+    for (int i = 0; i < k; ++i) {
+      float v = r0;
+      int who = lane;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, v, o);
+        const int ow = __shfl_xor_sync(kFull, who, o);
+        if (ov < v || (ov == v && ow < who)) { v = ov; who = ow; }
+      }
+      tau = v;
+      if (lane == who) { r0 = r1; r1 = r2; r2 = r3; r3 = INFINITY; }
+    }
+    thr = __fadd_rn(tau, __fmul_rn(2.f, eps));
+  }
+  int cnt = 0, ncand = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    bool broken = false;
+    cnt = 0;
+    ncand = 0;
+    for (int64_t b = 0; b < m; b += 32) {
+      const int64_t j = b + lane;
+      const float v = j < m ? a[j] : INFINITY;
+      const bool cand = j < m && !(v > thr);
+      const uint32_t cm = __ballot_sync(kFull, cand);
+      if (!cm) continue;
+      const int nc = __popc(cm);
+      ncand += nc;
+      if (cand) {
+        const int pos = __popc(cm & lanemask_lt());
+        S.cid[pos] = (uint32_t)ids[j];
+        S.ck1[pos] = f2u(v);   // its approximation, for the bound check
+      }
+      __syncwarp();
+      const bool full = cnt == k;
+      const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
+      const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
+      const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+      uint64_t ck = kNoKey;
+      uint32_t cv = kEmptySlot;
+      if (lane < nc) {
+        if (thr != INFINITY && !(fabsf(__fsub_rn(u2f(S.ck1[lane]), dist)) <= eps)) broken = true;
+        ck = make_key(0u, dist);
+        cv = S.cid[lane];
+        if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+      }
+      int r0;
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+    }
+    if (!__any_sync(kFull, broken)) break;
+    if (lane == 0) atomicOr(status, kErrTcBound);
+    thr = INFINITY;   // the bound failed on a candidate: every row is a candidate
+  }
+  write_answers(S, cnt, qi, k, out_ids, out_dist);
+  if (counters && lane == 0) {
+    int32_t *c = counters + qi * 4;
+    c[0] = 0; c[1] = ncand; c[2] = (int32_t)m; c[3] = 1;
+  }
+}
+
+__global__ void row_norms_kernel(DevIndex ix, float *xn, unsigned int *xmax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ix.n) return;
+  const float *r = ix.x + i * ix.xs;
+  float acc = 0.f;
+  for (int e = 0; e < ix.d; ++e) acc = __fmaf_rn(r[e], r[e], acc);
+  xn[i] = acc;
+  atomicMax(xmax, f2u(acc));   // non-negative floats order as their bit patterns
+}
+
+template <int CAP, int P, int CPL>
+cudaError_t launch_select(const SearchLaunch &L) {
+  const size_t sm = (size_t)kSearchWarps * warp_smem_bytes(list_slots(L.k), 5);
+  auto kern = tc_select_kernel<CAP, P, CPL>;
+  if (blocks_per_sm(kern, sm) == 0) return cudaErrorInvalidConfiguration;
+  kern<<<(unsigned)((L.nq + kSearchWarps - 1) / kSearchWarps), kSearchWarps * 32, sm, L.stream>>>(
+      L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, L.nq, L.k, L.tc.approx, L.out_ids, L.out_dist,
+      L.counters, L.status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_table_slots(int64_t nq) {
+  size_t h = 64;
+  while (h < (size_t)std::max<int64_t>(nq, 1) * 2) h <<= 1;
+  return h;
+}
+
+cudaError_t row_norms(const DevIndex &ix, float *xn, unsigned int *dmax, float *xmax_host, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned int), stream);
+  if (e != cudaSuccess) return e;
+  row_norms_kernel<<<(unsigned)((ix.n + 255) / 256), 256, 0, stream>>>(ix, xn, dmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  unsigned int hmax = 0;
+  if ((e = cudaMemcpyAsync(&hmax, dmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return e;
+  float f;
+  memcpy(&f, &hmax, sizeof(f));
+  *xmax_host = f;
+  return cudaSuccess;
+}
+
+cudaError_t launch_scan_tc(const SearchLaunch &L) {
+  const TcScratch &T = L.tc;
+  const int64_t nq = L.nq;
+  cudaError_t e;
+  const size_t H = T.slots;
+  if ((e = cudaMemsetAsync(T.hkey, 0xFF, H * sizeof(uint64_t), L.stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(T.hcnt, 0, H * sizeof(int32_t), L.stream)) != cudaSuccess) return e;
+  const unsigned qb = (unsigned)((nq + 255) / 256);
+  tc_group_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.filters, nq, T.hkey, T.hcnt, T.hrep, (uint32_t)(H - 1),
+                                            T.gslot, T.gmem);
+  tc_layout_kernel<<<1, kTcLayoutThreads, 0, L.stream>>>(L.ix, L.filters, L.plans, L.lists, L.cap, T.hcnt, T.hrep,
+                                                         (int64_t)H, T.hoff, T.gl, T.ioff, L.work + 4);
+  tc_member_kernel<<<qb, 256, 0, L.stream>>>(nq, T.gslot, T.gmem, T.hoff, T.members);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int bps = blocks_per_sm(tc_contract_kernel, kTcSmem, kTcThreads / 32);
+  if (bps == 0) return cudaErrorInvalidConfiguration;
+  tc_contract_kernel<<<(unsigned)(bps * num_sms()), kTcThreads, kTcSmem, L.stream>>>(
+      L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, T.hcnt, T.hrep, T.hoff, T.gl, T.ioff, T.members,
+      L.work + 4, T.approx, L.status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int P, CPL;
+  if (!row_mapping(L.ix.nchunks, &P, &CPL)) return cudaErrorInvalidValue;
+#define JAG_SCASE(CC, PP, QQ) \
+  if (list_capacity(L.k) == CC && P == PP && CPL == QQ) return launch_select<CC, PP, QQ>(L);
+#define JAG_SROWS(CC) JAG_SCASE(CC, 8, 1) JAG_SCASE(CC, 16, 1) JAG_SCASE(CC, 32, 1) JAG_SCASE(CC, 32, 2) \
+  JAG_SCASE(CC, 32, 4) JAG_SCASE(CC, 32, 8)
+  JAG_SROWS(64)
+  JAG_SROWS(128)
+  JAG_SROWS(256)
+#undef JAG_SROWS
+#undef JAG_SCASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace jag

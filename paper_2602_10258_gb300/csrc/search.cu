@@ -509,12 +509,13 @@ int scan_rows_per_round(int64_t xs) {
 }
 
 SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_bytes, int64_t cap, int32_t k,
-                                    int32_t ls, int scan_all, int64_t s0) {
-  SearchScratch s;
+                                    int32_t ls, int scan_all, int64_t s0, int tc) {
+  SearchScratch s{};
   const size_t q1 = (size_t)std::max<int64_t>(nq, 1);
   scan_tiling(ix.n, scan_all, s0, cap, &s.ntiles, &s.tile);
   const bool lists = !scan_all && s0 > 0 && ix.a_mask != nullptr;
-  const bool scans = scan_all || s0 > 0;
+  s.tc = (!scan_all && s0 > 0 && tc) ? 1 : 0;
+  const bool parts_needed = scan_all || (s0 > 0 && !s.tc);
   size_t off = 0;
   s.plans = off; off += align256(sizeof(QueryPlan) * q1);
   s.lut = off; off += align256((size_t)std::max<int64_t>(aux_bytes, 1) * 8);
@@ -522,12 +523,26 @@ SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_
   s.list_counts = off; off += align256(q1 * 4);
   s.work = off; off += 256;
   s.status = off; off += 256;
-  const size_t parts = scans ? q1 * (size_t)s.ntiles * (size_t)k : 1;
+  const size_t parts = parts_needed ? q1 * (size_t)s.ntiles * (size_t)k : 1;
   s.part_key = off; off += align256(parts * 8);
   s.part_id = off; off += align256(parts * 4);
-  s.scan_items = off; off += (!scan_all && s0 > 0) ? align256(q1 * (size_t)s.ntiles * 8) : 256;
+  s.scan_items = off; off += (!scan_all && s0 > 0 && !s.tc) ? align256(q1 * (size_t)s.ntiles * 8) : 256;
   s.rr = ix.fmt != JAG_VEC_F32 ? rerank_count(k, ls) : 0;
   s.rr_ids = off; off += align256(q1 * (size_t)std::max(s.rr, 1) * 4);
+  if (s.tc) {
+    const size_t H = tc_table_slots(nq);
+    s.slots = H;
+    s.approx = off; off += align256(q1 * (size_t)cap * 4);
+    s.hkey = off; off += align256(H * 8);
+    s.hcnt = off; off += align256(H * 4);
+    s.hrep = off; off += align256(H * 4);
+    s.hoff = off; off += align256(H * 4);
+    s.gl = off; off += align256(H * 4);
+    s.ioff = off; off += align256(H * 8);
+    s.gslot = off; off += align256(q1 * 4);
+    s.gmem = off; off += align256(q1 * 4);
+    s.members = off; off += align256(q1 * 4);
+  }
   s.total = off;
   return s;
 }
@@ -546,6 +561,20 @@ void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base) {
   L.tile = s.tile;
   L.rr = s.rr;
   L.rr_ids = reinterpret_cast<int32_t *>(base + s.rr_ids);
+  L.tc = TcScratch{};
+  if (s.tc) {
+    L.tc.approx = reinterpret_cast<float *>(base + s.approx);
+    L.tc.hkey = reinterpret_cast<uint64_t *>(base + s.hkey);
+    L.tc.hcnt = reinterpret_cast<int32_t *>(base + s.hcnt);
+    L.tc.hrep = reinterpret_cast<int32_t *>(base + s.hrep);
+    L.tc.hoff = reinterpret_cast<int32_t *>(base + s.hoff);
+    L.tc.gl = reinterpret_cast<int32_t *>(base + s.gl);
+    L.tc.ioff = reinterpret_cast<int64_t *>(base + s.ioff);
+    L.tc.gslot = reinterpret_cast<int32_t *>(base + s.gslot);
+    L.tc.gmem = reinterpret_cast<int32_t *>(base + s.gmem);
+    L.tc.members = reinterpret_cast<int32_t *>(base + s.members);
+    L.tc.slots = s.slots;
+  }
 }
 
 template <int CAP, int P, int CPL>
@@ -699,7 +728,7 @@ cudaError_t run_search(const SearchLaunch &L) {
     S.stream = side;
     S.ev_begin = S.ev_end = nullptr;
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
-    if (e == cudaSuccess) e = dispatch_job(S, P, CPL, kJobScan, L.k);
+    if (e == cudaSuccess) e = L.tc.approx ? launch_scan_tc(S) : dispatch_job(S, P, CPL, kJobScan, L.k);
     if (e == cudaSuccess) e = cudaEventRecord(ev_join, side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(L.stream, ev_join, 0);
     cudaEventDestroy(ev_fork);
@@ -707,7 +736,7 @@ cudaError_t run_search(const SearchLaunch &L) {
     return e;
   }
   if (e != cudaSuccess) return e;
-  if (L.s0 > 0) return dispatch_job(L, P, CPL, kJobScan, L.k);
+  if (L.s0 > 0) return L.tc.approx ? launch_scan_tc(L) : dispatch_job(L, P, CPL, kJobScan, L.k);
   return cudaSuccess;
 }
 

@@ -333,3 +333,22 @@ def test_flat_query_call(label_case):
     torch.cuda.synchronize()
     rid, rd, rc = O.query(ix, w.q, w.filters, w.aux, 10, 48, s0=2048, scan_cap=8192)
     assert_parity(ids.cpu().numpy(), dist.cpu().numpy(), rid, rd, "jag_query")
+
+
+@pytest.mark.parametrize("case", ["label_case", "subset_case", "mixed_case"])
+def test_tensor_core_scan_preselects(case, request):
+    """Scan-routed queries go through the tensor-core contraction: only the
+    rows within the approximation threshold get an exact distance (counter
+    1), far fewer than the passing set (counter 2), and the answers are the
+    oracle's exact filtered k-NN."""
+    w, ix, _, gi = request.getfixturevalue(case)
+    ids, dist, cnt, = jag.jag_search_host(gi.h, w.q, w.filters, w.aux, 10, 48, counters=True, s0=4000,
+                                          scan_cap=8192)
+    routed = np.nonzero(cnt[:, 3] == 1)[0]
+    assert len(routed) > 0
+    bi, bd, _, _ = O.brute_force(ix, w.q[routed], w.filters[routed], w.aux, 10)
+    assert (ids[routed] == bi).all() and np.array_equal(dist[routed].view(np.uint32), bd.view(np.uint32))
+    big = routed[cnt[routed, 2] > 200]
+    if len(big):
+        assert (cnt[big, 1] < cnt[big, 2]).mean() > 0.9
+        assert cnt[big, 1].mean() < 0.5 * cnt[big, 2].mean()

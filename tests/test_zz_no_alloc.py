@@ -14,6 +14,8 @@ parity tolerance (they are in fact identical).  A repeated call must leave
 the device's free memory and torch's allocator unchanged.  This file sorts
 last, so that a stop at the first failure has already run every other test;
 it also passes when run on its own."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -101,6 +103,7 @@ def test_repeated_call_allocates_nothing(index_and_inputs):
     w, gi, q, f, aux = index_and_inputs
     out = _outputs(q.shape[0], 10, q.device)
     _run(jag.jag_search_noalloc, gi, q, f, aux, 10, 64, 300, 1024, out=out)     # warm-up: loads kernel code
+    gc.collect()                     # earlier tests' garbage must not be freed inside the measured window
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
     alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
