@@ -9,14 +9,14 @@
 namespace jag {
 
 // Scratch of the tensor-core exact scan (scan_tc.cu): approximate distances
-// [nq][cap], the grouping hash table (slots entries) and the group members.
+// [nq][cap]; per tile of the two sorted columns (2 T0 tiles, T0 = ceil(n /
+// 128)) the count, fill and first entry of its query list; the lists (tq);
+// per work unit (2 T0 tiles, then nq queries) the first work item; block
+// sums of the unit scan.
 struct TcScratch {
   float *approx;
-  uint64_t *hkey;
-  int32_t *hcnt, *hrep, *hoff, *gl;
-  int64_t *ioff;
-  int32_t *gslot, *gmem, *members;
-  size_t slots;
+  int32_t *tcnt, *tfill, *toff, *tq;
+  int64_t *ioff, *bsum;
 };
 
 // One jag_search call, resolved to device pointers.
@@ -71,7 +71,7 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L);
 // regions replace the fp32 scan's partial lists and work items.
 struct SearchScratch {
   size_t plans, lut, lists, list_counts, work, status, part_key, part_id, scan_items, rr_ids;
-  size_t approx, hkey, hcnt, hrep, hoff, gl, ioff, gslot, gmem, members, slots;
+  size_t approx, tcnt, tfill, toff, tq, ioff, bsum;
   size_t total;
   int32_t rr, ntiles, tc;
   int64_t tile;
@@ -98,8 +98,8 @@ cudaError_t run_search(const SearchLaunch &L);
 
 // The tensor-core exact scan of the scan-routed queries (scan_tc.cu).
 cudaError_t launch_scan_tc(const SearchLaunch &L);
-// Hash-table slots of the scan's grouping for nq queries: a power of two >= 2 nq.
-size_t tc_table_slots(int64_t nq);
+// Tiles of 128 positions of a sorted column of n points.
+int64_t tc_column_tiles(int64_t n);
 // |x|^2 of every row into xn and their maximum into *xmax_host (dmax: one
 // device word of scratch); synchronous on stream.
 cudaError_t row_norms(const DevIndex &ix, float *xn, unsigned int *dmax, float *xmax_host, cudaStream_t stream);

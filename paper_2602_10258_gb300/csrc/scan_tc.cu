@@ -1,20 +1,22 @@
 // Exact pre-filter scan on the tensor cores (the Pre-Filtering baseline of
 // the experiments, for the queries routed to the scan).
 //
-// Queries whose passing sets are the same slice of a sorted column (every
-// query of one label, say) share their rows, so a group's distances form one
-// dense contraction: rows x queries over the dimension.  The scan runs in
-// three steps:
+// Queries routed to the scan that share rows -- every query of one label
+// shares its whole slice of the sorted column, overlapping ranges share part
+// of theirs -- form dense contractions: rows x queries over the dimension.
+// The scan runs in three steps:
 //
-//  1. grouping   scan-routed queries are grouped by passing set (the slice's
-//                bounds; a gathered subset / boolean list is a group of its
-//                own) with a hash table in device memory;
-//  2. contract   a CTA takes 128 rows of a group and up to 64 of its queries,
-//                gathers the fp32 rows and queries into shared memory in the
-//                tensor core's K-major layout, and computes all dot products
-//                with tcgen05.mma (kind::tf32, accumulators in tensor
-//                memory); the epilogue writes the approximate squared
-//                distance a = |x|^2 + |q|^2 - 2 q.x of every (query, row);
+//  1. grouping   the sorted columns are cut into tiles of 128 positions;
+//                every slice-routed query is listed at each tile its slice
+//                touches (a counting sort by tile); a gathered subset /
+//                boolean passing set is cut into tiles of its own;
+//  2. contract   a CTA takes one tile (128 rows) and up to 64 of the queries
+//                listed there, gathers the fp32 rows and queries into shared
+//                memory in the tensor core's K-major layout, and computes all
+//                dot products with tcgen05.mma (kind::tf32, accumulators in
+//                tensor memory); the epilogue writes the approximate squared
+//                distance a = |x|^2 + |q|^2 - 2 q.x of every row inside the
+//                query's slice;
 //  3. select     one warp per query finds a threshold tau that at least k
 //                rows reach (the k-th smallest of a sample of the a values),
 //                computes the canonical fp32 distance of every row with
@@ -101,55 +103,49 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-__device__ __forceinline__ uint64_t mix64(uint64_t v) {
-  v ^= v >> 33; v *= 0xFF51AFD7ED558CCDull; v ^= v >> 33; v *= 0xC4CEB9FE1A85EC53ull; v ^= v >> 33;
-  return v;
-}
-
-// The group key of a scan-routed query: its slice (column, begin, end), or,
-// for a gathered list, the query itself.
-__device__ __forceinline__ uint64_t group_key(const QueryPlan &pl, int32_t kind, int64_t qi) {
-  if (pl.route == kRouteSlice)
-    return ((uint64_t)(kind == JAG_F_RANGE_F32 ? 1 : 0) << 62) | ((uint64_t)pl.begin << 31) | (uint64_t)pl.end;
-  return (1ull << 63) | (uint64_t)qi;
-}
-
 __device__ __forceinline__ bool scan_routed(int32_t route) { return route == kRouteSlice || route == kRouteList; }
 
-__device__ __forceinline__ void group_rows(const DevIndex &ix, const jag_filter *filters, const QueryPlan &pl,
-                                           int64_t qi, const int32_t *lists, int64_t cap, const int32_t **ids,
-                                           int64_t *m) {
-  if (pl.route == kRouteSlice) {
-    *ids = (filters[qi].kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
-    *m = pl.end - pl.begin;
-  } else {
-    *ids = lists + qi * cap;
-    *m = pl.count;
-  }
-}
+// The sorted column a slice-routed query reads: 0 = int32, 1 = float32.
+__device__ __forceinline__ int slice_column(int32_t kind) { return kind == JAG_F_RANGE_F32 ? 1 : 0; }
 
-// (1a) every scan-routed query joins the group of its key.
-__global__ void tc_group_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, uint64_t *hkey,
-                                int32_t *hcnt, int32_t *hrep, uint32_t hmask, int32_t *gslot, int32_t *gmem) {
-  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Work units of the scan: U = 2 T0 column tiles (T0 = ceil(n / 128) per
+// column), then one unit per query (its gathered list, if list-routed).
+struct TcUnits {
+  int64_t T0, U;
+};
+
+// (1a) each slice-routed query counts itself at every tile its slice touches
+// (one warp per query, lanes over tiles).
+__global__ void tc_count_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, int64_t T0,
+                                int32_t *tcnt) {
+  const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (qi >= nq) return;
   const QueryPlan pl = plans[qi];
-  if (!scan_routed(pl.route)) { gslot[qi] = -1; return; }
-  const uint64_t key = group_key(pl, filters[qi].kind, qi);
-  uint32_t h = (uint32_t)mix64(key) & hmask;
-  for (uint32_t probe = 0; probe <= hmask; ++probe) {   // the table has at least 2 nq slots
-    const unsigned long long old = atomicCAS((unsigned long long *)&hkey[h], ~0ull, (unsigned long long)key);
-    if (old == ~0ull || old == key) break;
-    h = (h + 1) & hmask;
-  }
-  const int32_t j = atomicAdd(&hcnt[h], 1);
-  if (j == 0) hrep[h] = (int32_t)qi;
-  gslot[qi] = (int32_t)h;
-  gmem[qi] = j;
+  if (pl.route != kRouteSlice || pl.end <= pl.begin) return;
+  const int64_t base = slice_column(filters[qi].kind) * T0;
+  for (int64_t t = pl.begin / kTcRows + lane; t <= (pl.end - 1) / kTcRows; t += 32) atomicAdd(&tcnt[base + t], 1);
 }
 
-// Inclusive block-wide sum of v over kTcLayoutThreads threads.
-constexpr int kTcLayoutThreads = 1024;
+// Per unit: (query entries of a column tile, work items).  A column tile has
+// one item per chunk of up to 64 listed queries; a list-routed query one
+// item per 128 rows of its list.
+__device__ __forceinline__ void unit_sizes(int64_t u, const TcUnits &tu, const int32_t *tcnt, const QueryPlan *plans,
+                                           int64_t *entries, int64_t *items) {
+  if (u < 2 * tu.T0) {
+    const int64_t c = tcnt[u];
+    *entries = c;
+    *items = (c + kTcQueries - 1) / kTcQueries;
+  } else {
+    const QueryPlan pl = plans[u - 2 * tu.T0];
+    *entries = 0;
+    *items = pl.route == kRouteList ? ((int64_t)pl.count + kTcRows - 1) / kTcRows : 0;
+  }
+}
+
+constexpr int kTcScanBlock = 1024;
+
+// Inclusive block-wide sum of v over kTcScanBlock threads.
 __device__ __forceinline__ int64_t block_scan_incl(int64_t v, int64_t *wsum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -174,53 +170,69 @@ __device__ __forceinline__ int64_t block_scan_incl(int64_t v, int64_t *wsum) {
   return r;
 }
 
-// (1b) one CTA numbers the groups (slot order), places their members
-// (hoff: first member position) and counts their work items: one per
-// (128-row tile, chunk of up to 64 queries); gl[g] = slot of group g,
-// ioff[g] = first item of group g; counters[0] = groups, counters[1] = items.
-__global__ void __launch_bounds__(kTcLayoutThreads)
-tc_layout_kernel(DevIndex ix, const jag_filter *filters, const QueryPlan *plans, const int32_t *lists, int64_t cap,
-                 const int32_t *hcnt, const int32_t *hrep, int64_t H, int32_t *hoff, int32_t *gl, int64_t *ioff,
-                 unsigned long long *counters) {
+// (1b) exclusive prefix sums of (entries, items) over the units, in three
+// passes: block totals, a scan of the block totals, block-local scans.
+__global__ void __launch_bounds__(kTcScanBlock)
+tc_sum_kernel(TcUnits tu, const int32_t *tcnt, const QueryPlan *plans, int64_t *bsum) {
   __shared__ int64_t wsum[32];
-  __shared__ int64_t tot[3];
-  int64_t ng = 0, nm = 0, ni = 0;
-  for (int64_t base = 0; base < H; base += kTcLayoutThreads) {
-    const int64_t s = base + threadIdx.x;
-    const int32_t c = s < H ? hcnt[s] : 0;
-    int64_t items = 0;
-    if (c > 0) {
-      const int32_t r = hrep[s];
-      const int32_t *ids;
-      int64_t m;
-      group_rows(ix, filters, plans[r], r, lists, cap, &ids, &m);
-      items = ((m + kTcRows - 1) / kTcRows) * ((c + kTcQueries - 1) / kTcQueries);
-    }
-    const int64_t g_incl = block_scan_incl(c > 0 ? 1 : 0, wsum);
-    const int64_t m_incl = block_scan_incl(c, wsum);
-    const int64_t i_incl = block_scan_incl(items, wsum);
-    if (c > 0) {
-      const int64_t g = ng + g_incl - 1;
-      gl[g] = (int32_t)s;
-      hoff[s] = (int32_t)(nm + m_incl - c);
-      ioff[g] = ni + i_incl - items;
-    }
-    // totals of this round: the last thread's inclusive sums
-    if (threadIdx.x == kTcLayoutThreads - 1) { tot[0] = g_incl; tot[1] = m_incl; tot[2] = i_incl; }
-    __syncthreads();
-    ng += tot[0]; nm += tot[1]; ni += tot[2];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) { counters[0] = (unsigned long long)ng; counters[1] = (unsigned long long)ni; }
+  const int64_t u = (int64_t)blockIdx.x * kTcScanBlock + threadIdx.x;
+  int64_t e = 0, i = 0;
+  if (u < tu.U) unit_sizes(u, tu, tcnt, plans, &e, &i);
+  const int64_t es = block_scan_incl(e, wsum);
+  const int64_t is = block_scan_incl(i, wsum);
+  if (threadIdx.x == kTcScanBlock - 1) { bsum[2 * blockIdx.x] = es; bsum[2 * blockIdx.x + 1] = is; }
 }
 
-// (1c) members of each group in consecutive positions.
-__global__ void tc_member_kernel(int64_t nq, const int32_t *gslot, const int32_t *gmem, const int32_t *hoff,
-                                 int32_t *members) {
-  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kTcScanBlock)
+tc_sum_blocks_kernel(int64_t nblk, int64_t *bsum, unsigned long long *counters) {
+  __shared__ int64_t wsum[32];
+  int64_t ce = 0, ci = 0;
+  for (int64_t b0 = 0; b0 < nblk; b0 += kTcScanBlock) {
+    const int64_t b = b0 + threadIdx.x;
+    const int64_t e = b < nblk ? bsum[2 * b] : 0, i = b < nblk ? bsum[2 * b + 1] : 0;
+    const int64_t es = block_scan_incl(e, wsum);
+    const int64_t is = block_scan_incl(i, wsum);
+    __syncthreads();
+    if (b < nblk) { bsum[2 * b] = ce + es - e; bsum[2 * b + 1] = ci + is - i; }
+    __shared__ int64_t tot[2];
+    if (threadIdx.x == kTcScanBlock - 1) { tot[0] = es; tot[1] = is; }
+    __syncthreads();
+    ce += tot[0];
+    ci += tot[1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { counters[0] = (unsigned long long)ce; counters[1] = (unsigned long long)ci; }
+}
+
+__global__ void __launch_bounds__(kTcScanBlock)
+tc_offsets_kernel(TcUnits tu, const int32_t *tcnt, const QueryPlan *plans, const int64_t *bsum, int32_t *toff,
+                  int64_t *ioff) {
+  __shared__ int64_t wsum[32];
+  const int64_t u = (int64_t)blockIdx.x * kTcScanBlock + threadIdx.x;
+  int64_t e = 0, i = 0;
+  if (u < tu.U) unit_sizes(u, tu, tcnt, plans, &e, &i);
+  const int64_t es = block_scan_incl(e, wsum);
+  const int64_t is = block_scan_incl(i, wsum);
+  if (u < tu.U) {
+    if (u < 2 * tu.T0) toff[u] = (int32_t)(bsum[2 * blockIdx.x] + es - e);
+    ioff[u] = bsum[2 * blockIdx.x + 1] + is - i;
+  }
+}
+
+// (1c) each slice-routed query enters the list of every tile its slice
+// touches.
+__global__ void tc_fill_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, int64_t T0,
+                               const int32_t *toff, int32_t *tfill, int32_t *tq) {
+  const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (qi >= nq) return;
-  const int32_t s = gslot[qi];
-  if (s >= 0) members[hoff[s] + gmem[qi]] = (int32_t)qi;
+  const QueryPlan pl = plans[qi];
+  if (pl.route != kRouteSlice || pl.end <= pl.begin) return;
+  const int64_t base = slice_column(filters[qi].kind) * T0;
+  for (int64_t t = pl.begin / kTcRows + lane; t <= (pl.end - 1) / kTcRows; t += 32) {
+    const int32_t pos = atomicAdd(&tfill[base + t], 1);
+    tq[toff[base + t] + pos] = (int32_t)qi;
+  }
 }
 
 // (2) the contraction.  Persistent CTAs of four warps claim work items; per
@@ -231,9 +243,9 @@ __global__ void tc_member_kernel(int64_t nq, const int32_t *gslot, const int32_t
 // approximate distances approx[q][position of the row in q's passing set].
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
-                   const int32_t *lists, int64_t cap, const int32_t *hcnt, const int32_t *hrep, const int32_t *hoff,
-                   const int32_t *gl, const int64_t *ioff, const int32_t *members, unsigned long long *counters,
-                   float *approx, uint32_t *status) {
+                   const int32_t *lists, int64_t cap, TcUnits tu, const int32_t *tcnt, const int32_t *toff,
+                   const int32_t *tq, const int64_t *ioff, unsigned long long *counters, float *approx,
+                   uint32_t *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float *sa = reinterpret_cast<float *>(smem);
@@ -242,6 +254,8 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
   __shared__ uint32_t s_taddr;
   __shared__ int64_t s_item;
   __shared__ int32_t s_qid[kTcQueries];
+  __shared__ int32_t s_qb[kTcQueries];   // first position of the row set in the query's own passing set
+  __shared__ int32_t s_qm[kTcQueries];   // rows of the query's passing set
   __shared__ float s_qn[kTcQueries];
   __shared__ int32_t s_rid[kTcRows];
   __shared__ int s_abort;
@@ -263,7 +277,7 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
   tc_fence_after();
   const uint32_t taddr = s_taddr;
   const uint32_t sa_addr = smem_u32(sa), sb_addr = smem_u32(sb);
-  const unsigned long long ng = counters[0], ni = counters[1];
+  const unsigned long long ni = counters[1];
   uint32_t phase = 0;
   const int nkc = (d + kTcK - 1) / kTcK;
   for (;;) {
@@ -272,27 +286,41 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
     const int64_t item = s_item;
     __syncthreads();   // every thread has read s_item before the next claim overwrites it
     if (item >= (int64_t)ni) break;
-    // the item's group: the last g with ioff[g] <= item
-    int64_t lo = 0, hi = (int64_t)ng - 1;
+    // the item's unit: the last u with ioff[u] <= item
+    int64_t lo = 0, hi = tu.U - 1;
     while (lo < hi) {
       const int64_t mid = (lo + hi + 1) >> 1;
       if (ioff[mid] <= item) lo = mid; else hi = mid - 1;
     }
-    const int32_t slot = gl[lo];
-    const int32_t nmem = hcnt[slot];
-    const int32_t rep = hrep[slot];
-    const int32_t *ids;
-    int64_t m;
-    group_rows(ix, filters, plans[rep], rep, lists, cap, &ids, &m);
-    const int64_t nchunk = (nmem + kTcQueries - 1) / kTcQueries;
     const int64_t local = item - ioff[lo];
-    const int64_t tile = local / nchunk, chunk = local % nchunk;
-    const int64_t r0 = tile * kTcRows;
-    const int nrow = (int)min64(kTcRows, m - r0);
-    const int nqc = (int)min64(kTcQueries, (int64_t)nmem - chunk * kTcQueries);
+    int nrow, nqc;
+    if (lo < 2 * tu.T0) {
+      // a tile of a sorted column and a chunk of the queries listed there;
+      // row r of the tile is position t * 128 + r of the column, which is
+      // position t * 128 + r - begin of a query's own slice
+      const int col = (int)(lo / tu.T0);
+      const int64_t t = lo - col * tu.T0;
+      const int32_t *sid = col ? ix.sf32_id : ix.si32_id;
+      nrow = (int)min64(kTcRows, ix.n - t * kTcRows);
+      nqc = (int)min64(kTcQueries, (int64_t)tcnt[lo] - local * kTcQueries);
+      if (tid < nqc) {
+        const int32_t qi = tq[toff[lo] + local * kTcQueries + tid];
+        const QueryPlan pl = plans[qi];
+        s_qid[tid] = qi;
+        s_qb[tid] = (int32_t)(t * kTcRows - pl.begin);
+        s_qm[tid] = (int32_t)(pl.end - pl.begin);
+      }
+      s_rid[tid] = tid < nrow ? sid[t * kTcRows + tid] : -1;
+    } else {
+      // 128 rows of one list-routed query's gathered passing set
+      const int64_t qi = lo - 2 * tu.T0;
+      const int32_t cnt = plans[qi].count;
+      nrow = (int)min64(kTcRows, (int64_t)cnt - local * kTcRows);
+      nqc = 1;
+      if (tid == 0) { s_qid[0] = (int32_t)qi; s_qb[0] = (int32_t)(local * kTcRows); s_qm[0] = cnt; }
+      s_rid[tid] = tid < nrow ? lists[qi * cap + local * kTcRows + tid] : -1;
+    }
     const int N = (nqc + 15) & ~15;
-    if (tid < kTcQueries) s_qid[tid] = tid < nqc ? members[hoff[slot] + chunk * kTcQueries + tid] : -1;
-    s_rid[tid] = tid < nrow ? ids[r0 + tid] : -1;
     __syncthreads();
     // |q|^2 of the chunk's queries, one warp per query
     for (int j = warp; j < nqc; j += kTcThreads / 32) {
@@ -383,9 +411,10 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int n = c0 + j;
-        if (n < nqc && r < nrow) {
+        const int pos = s_qb[n < kTcQueries ? n : 0] + r;   // the row's position in the query's passing set
+        if (n < nqc && r < nrow && pos >= 0 && pos < s_qm[n]) {
           const float a = __fsub_rn(__fadd_rn(xn, s_qn[n]), __fmul_rn(2.f, u2f(v[j])));
-          approx[(int64_t)s_qid[n] * cap + r0 + r] = a;
+          approx[(int64_t)s_qid[n] * cap + pos] = a;
         }
       }
     }
@@ -398,6 +427,18 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
   tc_fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+}
+
+__device__ __forceinline__ void group_rows(const DevIndex &ix, const jag_filter *filters, const QueryPlan &pl,
+                                           int64_t qi, const int32_t *lists, int64_t cap, const int32_t **ids,
+                                           int64_t *m) {
+  if (pl.route == kRouteSlice) {
+    *ids = (slice_column(filters[qi].kind) ? ix.sf32_id : ix.si32_id) + pl.begin;
+    *m = pl.end - pl.begin;
+  } else {
+    *ids = lists + qi * cap;
+    *m = pl.count;
+  }
 }
 
 // (3) selection per scan-routed query (one warp each), see the file comment.
@@ -524,12 +565,6 @@ cudaError_t launch_select(const SearchLaunch &L) {
 
 }  // namespace
 
-size_t tc_table_slots(int64_t nq) {
-  size_t h = 64;
-  while (h < (size_t)std::max<int64_t>(nq, 1) * 2) h <<= 1;
-  return h;
-}
-
 cudaError_t row_norms(const DevIndex &ix, float *xn, unsigned int *dmax, float *xmax_host, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned int), stream);
   if (e != cudaSuccess) return e;
@@ -544,25 +579,30 @@ cudaError_t row_norms(const DevIndex &ix, float *xn, unsigned int *dmax, float *
   return cudaSuccess;
 }
 
+int64_t tc_column_tiles(int64_t n) { return (n + kTcRows - 1) / kTcRows; }
+
 cudaError_t launch_scan_tc(const SearchLaunch &L) {
   const TcScratch &T = L.tc;
   const int64_t nq = L.nq;
   cudaError_t e;
-  const size_t H = T.slots;
-  if ((e = cudaMemsetAsync(T.hkey, 0xFF, H * sizeof(uint64_t), L.stream)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(T.hcnt, 0, H * sizeof(int32_t), L.stream)) != cudaSuccess) return e;
-  const unsigned qb = (unsigned)((nq + 255) / 256);
-  tc_group_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.filters, nq, T.hkey, T.hcnt, T.hrep, (uint32_t)(H - 1),
-                                            T.gslot, T.gmem);
-  tc_layout_kernel<<<1, kTcLayoutThreads, 0, L.stream>>>(L.ix, L.filters, L.plans, L.lists, L.cap, T.hcnt, T.hrep,
-                                                         (int64_t)H, T.hoff, T.gl, T.ioff, L.work + 4);
-  tc_member_kernel<<<qb, 256, 0, L.stream>>>(nq, T.gslot, T.gmem, T.hoff, T.members);
+  TcUnits tu;
+  tu.T0 = tc_column_tiles(L.ix.n);
+  tu.U = 2 * tu.T0 + nq;
+  const int64_t nblk = (tu.U + kTcScanBlock - 1) / kTcScanBlock;
+  if ((e = cudaMemsetAsync(T.tcnt, 0, sizeof(int32_t) * 2 * (size_t)tu.T0, L.stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(T.tfill, 0, sizeof(int32_t) * 2 * (size_t)tu.T0, L.stream)) != cudaSuccess) return e;
+  const unsigned wb = (unsigned)((nq * 32 + 255) / 256);   // one warp per query
+  tc_count_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.filters, nq, tu.T0, T.tcnt);
+  tc_sum_kernel<<<(unsigned)nblk, kTcScanBlock, 0, L.stream>>>(tu, T.tcnt, L.plans, T.bsum);
+  tc_sum_blocks_kernel<<<1, kTcScanBlock, 0, L.stream>>>(nblk, T.bsum, L.work + 4);
+  tc_offsets_kernel<<<(unsigned)nblk, kTcScanBlock, 0, L.stream>>>(tu, T.tcnt, L.plans, T.bsum, T.toff, T.ioff);
+  tc_fill_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.filters, nq, tu.T0, T.toff, T.tfill, T.tq);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int bps = blocks_per_sm(tc_contract_kernel, kTcSmem, kTcThreads / 32);
   if (bps == 0) return cudaErrorInvalidConfiguration;
   tc_contract_kernel<<<(unsigned)(bps * num_sms()), kTcThreads, kTcSmem, L.stream>>>(
-      L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, T.hcnt, T.hrep, T.hoff, T.gl, T.ioff, T.members,
-      L.work + 4, T.approx, L.status);
+      L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, tu, T.tcnt, T.toff, T.tq, T.ioff, L.work + 4,
+      T.approx, L.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int P, CPL;
   if (!row_mapping(L.ix.nchunks, &P, &CPL)) return cudaErrorInvalidValue;

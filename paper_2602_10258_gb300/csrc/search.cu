@@ -515,6 +515,10 @@ SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_
   scan_tiling(ix.n, scan_all, s0, cap, &s.ntiles, &s.tile);
   const bool lists = !scan_all && s0 > 0 && ix.a_mask != nullptr;
   s.tc = (!scan_all && s0 > 0 && tc) ? 1 : 0;
+  // a slice of at most cap rows touches at most cap / 128 + 2 tiles; the
+  // tile lists are indexed with int32, else the fp32 scan kernels run
+  const size_t tc_entries = q1 * ((size_t)cap / 128 + 2);
+  if (tc_entries >= ((size_t)1 << 31)) s.tc = 0;
   const bool parts_needed = scan_all || (s0 > 0 && !s.tc);
   size_t off = 0;
   s.plans = off; off += align256(sizeof(QueryPlan) * q1);
@@ -530,18 +534,14 @@ SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_
   s.rr = ix.fmt != JAG_VEC_F32 ? rerank_count(k, ls) : 0;
   s.rr_ids = off; off += align256(q1 * (size_t)std::max(s.rr, 1) * 4);
   if (s.tc) {
-    const size_t H = tc_table_slots(nq);
-    s.slots = H;
+    const size_t T0 = (size_t)tc_column_tiles(ix.n), U = 2 * T0 + q1;
     s.approx = off; off += align256(q1 * (size_t)cap * 4);
-    s.hkey = off; off += align256(H * 8);
-    s.hcnt = off; off += align256(H * 4);
-    s.hrep = off; off += align256(H * 4);
-    s.hoff = off; off += align256(H * 4);
-    s.gl = off; off += align256(H * 4);
-    s.ioff = off; off += align256(H * 8);
-    s.gslot = off; off += align256(q1 * 4);
-    s.gmem = off; off += align256(q1 * 4);
-    s.members = off; off += align256(q1 * 4);
+    s.tcnt = off; off += align256(2 * T0 * 4);
+    s.tfill = off; off += align256(2 * T0 * 4);
+    s.toff = off; off += align256(2 * T0 * 4);
+    s.tq = off; off += align256(tc_entries * 4);
+    s.ioff = off; off += align256(U * 8);
+    s.bsum = off; off += align256(((U + 1023) / 1024) * 16);
   }
   s.total = off;
   return s;
@@ -564,16 +564,12 @@ void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base) {
   L.tc = TcScratch{};
   if (s.tc) {
     L.tc.approx = reinterpret_cast<float *>(base + s.approx);
-    L.tc.hkey = reinterpret_cast<uint64_t *>(base + s.hkey);
-    L.tc.hcnt = reinterpret_cast<int32_t *>(base + s.hcnt);
-    L.tc.hrep = reinterpret_cast<int32_t *>(base + s.hrep);
-    L.tc.hoff = reinterpret_cast<int32_t *>(base + s.hoff);
-    L.tc.gl = reinterpret_cast<int32_t *>(base + s.gl);
+    L.tc.tcnt = reinterpret_cast<int32_t *>(base + s.tcnt);
+    L.tc.tfill = reinterpret_cast<int32_t *>(base + s.tfill);
+    L.tc.toff = reinterpret_cast<int32_t *>(base + s.toff);
+    L.tc.tq = reinterpret_cast<int32_t *>(base + s.tq);
     L.tc.ioff = reinterpret_cast<int64_t *>(base + s.ioff);
-    L.tc.gslot = reinterpret_cast<int32_t *>(base + s.gslot);
-    L.tc.gmem = reinterpret_cast<int32_t *>(base + s.gmem);
-    L.tc.members = reinterpret_cast<int32_t *>(base + s.members);
-    L.tc.slots = s.slots;
+    L.tc.bsum = reinterpret_cast<int64_t *>(base + s.bsum);
   }
 }
 
