@@ -41,8 +41,8 @@ R = 32
 LB = 64
 THRESHOLDS = (100, 0)
 ALPHA = 1.2
-S0 = 8192          # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
-SCAN_CAP = 8192
+S0 = 16384         # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
+SCAN_CAP = 16384
 
 
 def workload_desc(n, d, nq):
@@ -60,7 +60,7 @@ def rank_env():
     return rank, world, local
 
 
-def recall_at_k(ids, gt_ids, gt_d, k=K):
+def recall_at_k(ids, gt_ids, gt_d=None, k=K):
     """Tie-tolerant recall@k: returned ids whose true distance is within the
     k-th true distance count as hits; divided by min(k, #passing)."""
     out = np.zeros(len(ids))
@@ -358,6 +358,10 @@ def run_ours(args):
         serving = measure_serving(jag, idx, w, chosen, band, gt_ids, gt_d, value / world)
         log("serving: %s" % {k: (v["p50_ms"], v["p99_ms"], v["achieved_qps"]) for k, v in serving.items() if isinstance(v, dict)})
 
+    mixed = None
+    if not args.no_mixed:
+        mixed = measure_mixed(args, local, flush, stream)
+
     cpu, ocnt = None, None
     if rank == 0 and not args.no_cpu:
         cpu, ocnt = cpu_baseline(w, idx, chosen, gt_ids, gt_d, budget_s=args.cpu_seconds)
@@ -404,6 +408,7 @@ def run_ours(args):
                 "recall": float(np.nanmean(e2e_rec))},
         "cpu_baseline": cpu,
         "forms": forms,
+        "learned_form_mixed": mixed,
         "serving": serving,
         "clocks": clk.summary(),
         # per step: prep, graph search, scan work items, scan tiles, scan merge
@@ -535,6 +540,285 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
             "ms_per_step": round(ms, 4), "recall": per, "mean_hops_graph_route": round(hops, 1),
             "train": {"queries": n_train, "epochs": 60, "final_loss": round(loss, 4), "seconds": round(train_s, 1)},
             "steps": steps}
+
+
+# ---------------------------------------------------------------------------
+# the learned form's workload: float ranges and boolean filters
+# ---------------------------------------------------------------------------
+
+MIXED_R = 64                    # out-degree of both graphs of the mixed workload
+MIXED_T_RANGE = (100, 10, 0)    # thresholds of the float-range graph
+MIXED_T_BOOL = (100, 1, 0)      # thresholds of the mask graph (Hamming dist_A)
+MIXED_LADDER = (32, 48, 64, 96, 128, 160, 192, 224, 256)
+MIXED_H0 = 16
+
+
+def mixed_selectivity(w, dev):
+    """Exact selectivity of every filter of a mixed workload: float ranges by
+    binary search in the sorted column, boolean filters by counting the
+    points' 3-bit patterns on the GPU (torch; bookkeeping, not the path)."""
+    import torch
+    from paper_2602_10258_gb300 import datagen as D
+    kind = w.filters["kind"]
+    sel = np.zeros(len(w.q))
+    rq = np.nonzero(kind == 3)[0]
+    srt = np.sort(w.attr_f32)
+    fl = D.filter_fields(w.filters)
+    sel[rq] = (np.searchsorted(srt, fl["f_hi"][rq], "right") - np.searchsorted(srt, fl["f_lo"][rq], "left")) / w.n
+    mt = torch.from_numpy(w.attr_mask.view(np.int64)).to(dev)
+    for i in np.nonzero(kind == 5)[0]:
+        vm = int(w.filters["payload"][i])
+        bits = [b for b in range(64) if vm >> b & 1]
+        pat = torch.zeros_like(mt)
+        for j, b in enumerate(bits):
+            pat |= ((mt >> b) & 1) << j
+        h = torch.bincount(pat, minlength=1 << len(bits)).cpu().numpy()
+        tt = w.aux[int(w.filters["aux_off"][i]):]
+        sel[i] = sum(h[s_] for s_ in range(1 << len(bits)) if tt[s_ >> 3] >> (s_ & 7) & 1) / w.n
+    return sel
+
+
+class MixedIndex:
+    """The two graphs of the mixed workload over one point set: float-range
+    filters search a graph built on the float attribute, boolean filters one
+    built on the bit mask (Hamming dist_A, Sec. 3.1), each query routed by its
+    filter kind.  The two searches of a batch run on two streams."""
+
+    def __init__(self, jag, w, storage, device, graphs=None):
+        kw = dict(attr_f32=w.attr_f32, attr_mask=w.attr_mask, R=MIXED_R, l_b=64, alpha=ALPHA, storage=storage,
+                  device=device)
+        if graphs is None:
+            self.ix = [jag.Index(w.x, dist_a=jag.JAG_F_RANGE_F32, thresholds=MIXED_T_RANGE, **kw),
+                       jag.Index(w.x, dist_a=jag.JAG_F_BOOL, thresholds=MIXED_T_BOOL, **kw)]
+        else:
+            self.ix = [jag.Index(w.x, dist_a=da, graph=g, entry=e, **kw)
+                       for da, (g, e) in zip((jag.JAG_F_RANGE_F32, jag.JAG_F_BOOL), graphs)]
+
+    def graphs(self):
+        return [(ix.graph(), ix.info()["entry"]) for ix in self.ix]
+
+    def build_seconds(self):
+        return [round(ix.info()["build_seconds"], 2) for ix in self.ix]
+
+    def close(self):
+        for ix in self.ix:
+            ix.close()
+
+
+class MixedBatch:
+    """Device inputs and outputs of a mixed batch, split by filter kind."""
+
+    def __init__(self, jag, w, dev):
+        import torch
+        kind = w.filters["kind"]
+        self.rows = [np.nonzero(kind == jag.JAG_F_RANGE_F32)[0], np.nonzero(kind == jag.JAG_F_BOOL)[0]]
+        self.q = [torch.from_numpy(np.ascontiguousarray(w.q[r])).to(dev) for r in self.rows]
+        self.f = [jag.filters_to_device(w.filters[r], dev) for r in self.rows]
+        self.aux = jag.aux_to_device(w.aux, dev)
+        self.ids = [torch.empty((len(r), K), dtype=torch.int32, device=dev) for r in self.rows]
+        self.dist = [torch.empty((len(r), K), dtype=torch.float32, device=dev) for r in self.rows]
+        self.cnt = [torch.empty((len(r), 4), dtype=torch.int32, device=dev) for r in self.rows]
+        self.streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        self.n = len(w.q)
+
+    def search(self, jag, mix, beams, policy=None, counters=False, stream=None, scan_all=False):
+        """Both kinds' searches, forked from `stream` onto two streams and
+        joined back (asynchronous)."""
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for g in range(2):
+            st = self.streams[g]
+            st.wait_event(fork)
+            if len(self.rows[g]) == 0:
+                continue
+            kw = dict(flags=jag.JAG_SEARCH_SCAN_ALL) if scan_all else dict(s0=S0, scan_cap=SCAN_CAP, policy=policy)
+            jag.jag_search(mix.ix[g].h, self.q[g], self.f[g], self.aux, K, K if scan_all else beams[g], self.ids[g],
+                           self.dist[g], self.cnt[g] if counters else None, st, **kw)
+            done = torch.cuda.Event()
+            done.record(st)
+            stream.wait_event(done)
+
+    def gather(self, what):
+        out = np.empty((self.n,) + tuple(what[0].shape[1:]), dtype=what[0].cpu().numpy().dtype)
+        for g in range(2):
+            out[self.rows[g]] = what[g].cpu().numpy()
+        return out
+
+
+def band_recalls(rec, band):
+    return {name: float(np.mean(rec[(band == j) & ~np.isnan(rec)])) for j, (_, _, name) in enumerate(BANDS)
+            if ((band == j) & ~np.isnan(rec)).any()}
+
+
+def mixed_graph_bytes(cnt, row_bytes, attr_bytes, R_=MIXED_R):
+    """Gather bytes of the graph searches from the kernels' own counters:
+    hops * R * 4 + first-seen neighbours * attribute bytes + distances *
+    row bytes, over graph-routed queries."""
+    g = cnt[:, 3] == 0
+    c = cnt[g].astype(np.int64)
+    return int((c[:, 0] * R_ * 4 + c[:, 1] * attr_bytes + c[:, 2] * row_bytes).sum())
+
+
+def measure_mixed(args, local, flush, stream):
+    """The learned form's workload (float ranges and 3-of-32 boolean filters,
+    N = 1M, d = 128): plain fixed-beam search (fp32 and BF16 rows; per graph
+    the smallest beam with recall@10 >= 0.95 in every band of its queries)
+    against BF16 rows with the learned beam / stop network, trained on the
+    GPU on traces of 100,000 training queries labelled with the smallest
+    ladder beam reaching recall 0.95."""
+    import torch
+    from paper_2602_10258_gb300 import datagen as D
+    from paper_2602_10258_gb300 import jag
+    from paper_2602_10258_gb300 import policy as PL
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    w = D.make_mixed(n=args.n, d=128, nq=args.nq, seed=args.seed)
+    wt = D.make_mixed(n=args.n, d=128, nq=args.mixed_train, seed=args.seed, query_seed=101)
+    sel = mixed_selectivity(w, dev)
+    band = band_of(sel)
+    mix32 = MixedIndex(jag, w, jag.JAG_VEC_F32, local)
+    graphs = mix32.graphs()
+    mix16 = MixedIndex(jag, w, jag.JAG_VEC_BF16, local, graphs=graphs)
+    prep_s = time.time() - t0
+    hb = MixedBatch(jag, w, dev)
+    hb.search(jag, mix32, (K, K), scan_all=True)
+    torch.cuda.synchronize()
+    gt_ids = hb.gather(hb.ids)
+    out = {"workload": "float range (width log-uniform 1e-4..1) and boolean (AND/OR of 3 of 32 Bernoulli(0.3) bits) "
+                       "filters, half each, N=%d d=128 fp32 GMM-100, %d queries, k=10" % (w.n, len(w.q)),
+           "graphs": "float-range graph R=%d T=%s%%, mask graph R=%d T=%s%% (Hamming dist_A), GPU build %s s"
+                     % (MIXED_R, list(MIXED_T_RANGE), MIXED_R, list(MIXED_T_BOOL), mix32.build_seconds()),
+           "queries_by_kind": {"range": int(len(hb.rows[0])), "bool": int(len(hb.rows[1]))},
+           "band_queries": {name: int((band == j).sum()) for j, (_, _, name) in enumerate(BANDS)}}
+
+    def timed(mix, beams, pol, steps):
+        for _ in range(3):
+            hb.search(jag, mix, beams, pol, stream=stream)
+        evs = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hb.search(jag, mix, beams, pol, stream=stream)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    def evaluate(mix, beams, pol):
+        hb.search(jag, mix, beams, pol, counters=True, stream=stream)
+        torch.cuda.synchronize()
+        ids, cnt = hb.gather(hb.ids), hb.gather(hb.cnt)
+        rec = recall_at_k(ids, gt_ids, None)
+        return band_recalls(rec, band), cnt
+
+    steps = min(args.steps, 50)
+    forms = {}
+    for fname, mix, row_bytes in (("fp32", mix32, 512), ("bf16", mix16, 256)):
+        beams = []
+        for g in range(2):
+            chosen = MIXED_LADDER[-1]
+            for beam in MIXED_LADDER:
+                bb = [MIXED_LADDER[-1], MIXED_LADDER[-1]]
+                bb[g] = beam
+                per, _ = evaluate(mix, bb, None)
+                gb = band_of(sel[hb.rows[g]])
+                rec_g = recall_at_k(hb.gather(hb.ids)[hb.rows[g]], gt_ids[hb.rows[g]], None)
+                if all(v >= 0.95 for v in band_recalls(rec_g, gb).values()):
+                    chosen = beam
+                    break
+            beams.append(chosen)
+        per, cnt = evaluate(mix, beams, None)
+        ms = timed(mix, beams, None, steps)
+        gbytes = mixed_graph_bytes(cnt[hb.rows[0]], row_bytes, 4) + mixed_graph_bytes(cnt[hb.rows[1]], row_bytes, 8)
+        forms["plain_" + fname] = {"beam_range": beams[0], "beam_bool": beams[1], "qps": round(hb.n / (ms / 1e3), 1),
+                                   "ms_per_step": round(ms, 4), "recall": per,
+                                   "mean_hops_graph_route": round(float(cnt[cnt[:, 3] == 0, 0].mean()), 1),
+                                   "gather_bytes_per_step": gbytes,
+                                   "gather_frac_of_hbm": round(gbytes / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)}
+        log("mixed plain %s: beams %s, %.0f QPS, %s" % (fname, beams, hb.n / (ms / 1e3), per))
+    # learned policy: traces of the training queries on the BF16 graphs (the
+    # graph-routed ones: scan-routed queries never reach the policy)
+    t1 = time.time()
+    tb = MixedBatch(jag, wt, dev)
+    tb.search(jag, mix16, (K, K), scan_all=True)
+    torch.cuda.synchronize()
+    gt_train = [tb.ids[g].cpu().numpy() for g in range(2)]
+    tb.search(jag, mix16, (MIXED_LADDER[-1], MIXED_LADDER[-1]), counters=True)
+    torch.cuda.synchronize()
+    base = (forms["plain_bf16"]["beam_range"], forms["plain_bf16"]["beam_bool"])
+    tr = []
+    for g in range(2):
+        gq = np.nonzero(tb.cnt[g].cpu().numpy()[:, 3] == 0)[0]
+        if len(gq) == 0:
+            continue
+        sel_q = torch.from_numpy(gq).to(dev)
+        fg = tb.f[g].view(-1, 16)[sel_q].reshape(-1)
+        # traced at the call beam the policy will run with (the features depend on it)
+        tr.append(PL.collect_traces(mix16.ix[g], tb.q[g][sel_q], fg, tb.aux, K, base[g], gt_train[g][gq],
+                                    ladder=MIXED_LADDER, h0=MIXED_H0))
+    traces = PL.concat_traces(tr)
+    trace_s = time.time() - t1
+    nl = len(MIXED_LADDER)
+    keep = ~np.isnan(traces.recall).any(1)
+    order = np.random.default_rng(0).permutation(np.nonzero(keep)[0])
+    X = torch.from_numpy(np.ascontiguousarray(traces.X[order])).to(dev)
+    t2 = time.time()
+    nets, cands = {}, []
+    for shift in (0, 1, 2):
+        # labels: the smallest ladder beam reaching recall 0.95, raised by
+        # `shift` ladder steps as a margin; stop target from the label beam's
+        # last change
+        y, tt = traces.labels(target=0.95, stop_margin=1.25, stop_extra=8)
+        y = np.minimum(y + shift, nl - 1).astype(np.int32)
+        params = torch.from_numpy(D.mlp_init_params(nl, shift)).to(dev)
+        loss = jag.Trainer(nl, params).run(X, torch.from_numpy(y[order]).to(dev),
+                                           torch.from_numpy(tt[order]).to(dev), epochs=args.mixed_epochs, batch=1024,
+                                           lr=2e-3, lam=0.25)
+        nets[shift] = (params, float(loss[-1]), np.bincount(y[keep], minlength=nl))
+        for tau in (0.0, 0.5, 1.0):
+            for scale in (0.0, 96.0):
+                pol = jag.Policy.learned(params, ladder=MIXED_LADDER, h0=MIXED_H0, tau=tau, stop_scale=scale)
+                per, cnt = evaluate(mix16, base, pol)
+                cands.append((shift, tau, scale, pol, per, cnt))
+    torch.cuda.synchronize()
+    train_s = time.time() - t2
+    ok = [c for c in cands if all(v >= 0.95 for v in c[4].values())]
+    best = None
+    for shift, tau, scale, pol, per, cnt in ok:
+        ms = timed(mix16, base, pol, steps)
+        if best is None or ms < best[0]:
+            best = (ms, shift, tau, scale, per, cnt)
+    learned = {"train": {"queries": int(len(wt.q)), "traced_graph_queries": int(keep.sum()),
+                         "label_beams": {str(MIXED_LADDER[c]): int(v) for c, v in enumerate(nets[0][2])},
+                         "epochs": args.mixed_epochs, "final_loss_by_shift": {str(k_): round(v[1], 4)
+                                                                           for k_, v in nets.items()},
+                         "trace_seconds": round(trace_s, 1), "train_and_select_seconds": round(train_s, 1)},
+               "candidates": [{"shift": c[0], "tau": c[1], "stop_scale": c[2],
+                               "mean_hops": round(float(c[5][c[5][:, 3] == 0, 0].mean()), 1),
+                               "min_band_recall": round(min(c[4].values()), 4)} for c in cands]}
+    if best is None:
+        learned["qps"] = None
+        learned["note"] = "no (label shift, tau, stop scale) reached recall 0.95 in every band"
+    else:
+        ms, shift, tau, scale, per, cnt = best
+        gbytes = mixed_graph_bytes(cnt[hb.rows[0]], 256, 4) + mixed_graph_bytes(cnt[hb.rows[1]], 256, 8)
+        learned.update({"base_beam_range": base[0], "base_beam_bool": base[1], "h0": MIXED_H0, "label_shift": shift,
+                        "tau": tau, "stop_scale": scale, "qps": round(hb.n / (ms / 1e3), 1),
+                        "ms_per_step": round(ms, 4), "recall": per,
+                        "mean_hops_graph_route": round(float(cnt[cnt[:, 3] == 0, 0].mean()), 1),
+                        "gather_bytes_per_step": gbytes,
+                        "gather_frac_of_hbm": round(gbytes / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)})
+    forms["bf16_learned"] = learned
+    log("mixed learned: %s" % {k: v for k, v in learned.items() if k in ("label_shift", "tau", "stop_scale", "qps",
+                                                                       "recall", "mean_hops_graph_route")})
+    out["forms"] = forms
+    out["prep_seconds"] = round(prep_s, 1)
+    mix32.close()
+    mix16.close()
+    return out
 
 
 def serve_saturation(jag, idx, w, beam, batch_qps, n_req=2000, offered=(0.6, 0.8, 1.0)):
@@ -818,6 +1102,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the learned form's mixed range / boolean workload")
+    ap.add_argument("--mixed-train", type=int, default=100_000, help="training queries of the learned form")
+    ap.add_argument("--mixed-epochs", type=int, default=40)
+    ap.add_argument("--mixed-only", action="store_true", help="only the mixed workload's forms (prints its JSON)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-beam", type=int, default=192)
     ap.add_argument("--ref-queries", type=int, default=200)
@@ -839,7 +1127,12 @@ def main():
         SCAN_CAP = args.scan_cap
     if args.warmup < 3:
         args.warmup = 3
-    if args.profile:
+    if args.mixed_only:
+        import torch
+        torch.cuda.set_device(0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(measure_mixed(args, 0, flush, torch.cuda.current_stream())))
+    elif args.profile:
         run_profile(args)
     elif args.serve_large:
         run_serve_large(args)

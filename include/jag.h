@@ -171,8 +171,10 @@ typedef struct jag_search_args {
   const uint8_t *filter_aux;   /* truth tables of boolean filters, or NULL     */
   int64_t aux_bytes;           /* bytes in filter_aux                          */
   int64_t nq;                  /* number of queries, >= 0                      */
-  int32_t k;                   /* answers per query, 1..beam                   */
-  int32_t beam;                /* l_s of Algorithm 1, k..256                   */
+  int32_t k;                   /* answers per query, 1..min(beam, 256)         */
+  int32_t beam;                /* l_s of Algorithm 1, k..512 (at most 256 with
+                                  a policy, and 512 only for rows of at most
+                                  512 bytes in their stored format)            */
   int32_t *out_ids;            /* [nq][k] point ids, -1 padded                 */
   float *out_dist;             /* [nq][k] squared L2 distances, +inf padded    */
   void *stream;                /* cudaStream_t, NULL = legacy default stream   */

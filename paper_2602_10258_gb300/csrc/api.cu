@@ -152,8 +152,9 @@ jag_status check_search_args(const jag_index *idx, const jag_search_args *a) {
   if (a->nq < 0) return fail(JAG_EINVAL, "nq < 0");
   if (a->nq > 0 && (!a->queries || !a->filters || !a->out_ids || !a->out_dist))
     return fail(JAG_EINVAL, "NULL query, filter or output pointer");
-  if (a->beam < 1 || a->beam > 256) return fail(JAG_EINVAL, "beam must be in [1, 256]");
-  if (a->k < 1 || a->k > a->beam) return fail(JAG_EINVAL, "k must be in [1, beam]");
+  if (a->beam < 1 || a->beam > 512) return fail(JAG_EINVAL, "beam must be in [1, 512]");
+  if (a->k < 1 || a->k > a->beam || a->k > 256) return fail(JAG_EINVAL, "k must be in [1, min(beam, 256)]");
+  if (a->policy && a->beam > 256) return fail(JAG_EINVAL, "a search with a policy takes beams of at most 256");
   if (a->aux_bytes < 0 || (a->aux_bytes > 0 && !a->filter_aux)) return fail(JAG_EINVAL, "bad filter_aux");
   if (a->nq > (int64_t)1 << 31) return fail(JAG_EINVAL, "nq too large");
   if (a->policy) {

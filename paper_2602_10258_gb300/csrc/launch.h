@@ -104,7 +104,7 @@ int64_t tc_column_tiles(int64_t n);
 // device word of scratch); synchronous on stream.
 cudaError_t row_norms(const DevIndex &ix, float *xn, unsigned int *dmax, float *xmax_host, cudaStream_t stream);
 
-// Smallest supported list capacity >= ls (64, 128 or 256); 0 if ls > 256.
+// Smallest supported list capacity >= ls (64, 128, 256 or 512); 0 if ls > 512.
 int list_capacity(int ls);
 // Lanes per row P and chunks per lane for a row of nchunks 16-byte chunks.
 bool row_mapping(int nchunks, int *P, int *CPL);

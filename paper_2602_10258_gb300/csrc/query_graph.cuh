@@ -63,23 +63,26 @@ query_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters
     if constexpr (POL == 1) {
       // the plain search loop up to hop h0, the decision outside it, then the
       // same loop again from where it stopped (one inlined copy of the loop,
-      // no call inside it); the network's scratch is the candidate arrays
-      // cid, ck1, free between hops
-      const int64_t est = (f.kind == JAG_F_SUBSET || f.kind == JAG_F_BOOL) ? (int64_t)pl.est * ix.n / sample
-                          : (f.kind == JAG_F_NONE ? ix.n : (int64_t)pl.est);
-      float *fo = pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr;
-      if (fo && lane < JAG_MLP_FEATURES) fo[lane] = 0.f;
+      // no call inside it).  Only the beam and the hop limit of the current
+      // phase stay live across the loop: the limit is h0 before the decision
+      // and never h0 after it (a stop at h0 ends the search at the decision),
+      // and the decision's inputs are read again when it is taken.  The
+      // network's scratch is the candidate arrays cid, ck1, free between hops.
       SearchCursor cur{0, 0};
       int lsq = ls, lim = pol.mode != JAG_POLICY_PLAIN ? pol.h0 : 0x7FFFFFFF;
-      bool decided = false;
+      if (pol.features && lane < JAG_MLP_FEATURES) pol.features[(int64_t)qi * JAG_MLP_FEATURES + lane] = 0.f;
       for (;;) {
         cnt = greedy_search<CAP, P, CPL, FMT, 0, true>(ix, key, q, lsq, hbits, S, sink, st, lim, &cur);
-        if (decided || st.hops < lim) break;
+        if (lim != pol.h0 || st.hops < lim) break;
         __syncwarp();
-        const PolicyOut o = policy_decide(pol, S, reinterpret_cast<float *>(S.cid), cnt, k, est, f.kind, ls, fo,
+        const QueryPlan pd = plans[qi];
+        const int32_t kind = filters[qi].kind;
+        const int64_t est = (kind == JAG_F_SUBSET || kind == JAG_F_BOOL) ? (int64_t)pd.est * ix.n / sample
+                            : (kind == JAG_F_NONE ? ix.n : (int64_t)pd.est);
+        const PolicyOut o = policy_decide(pol, S, reinterpret_cast<float *>(S.cid), cnt, k, est, kind, ls,
+                                          pol.features ? pol.features + (int64_t)qi * JAG_MLP_FEATURES : nullptr,
                                           pol.forced ? pol.forced + (int64_t)qi * 2 : nullptr);
         __syncwarp();
-        decided = true;
         lsq = o.beam;
         if (cnt > lsq) cnt = lsq;
         if (o.stop > 0 && st.hops >= o.stop) break;
@@ -150,6 +153,13 @@ template <int CAP, int FMT, int POL>
 static cudaError_t launch_graph_cap(const SearchLaunch &L, int P, int CPL) {
 #define JAG_GCASE(PP, CC) \
   if (P == PP && CPL == CC) return launch_graph_one<CAP, PP, CC, FMT, POL>(L);
+  if constexpr (CAP == 512) {
+    // the 512-entry list: plain search of rows of at most 32 chunks
+    JAG_GCASE(8, 1)
+    JAG_GCASE(16, 1)
+    JAG_GCASE(32, 1)
+    return cudaErrorInvalidValue;
+  }
   JAG_GCASE(8, 1)
   JAG_GCASE(16, 1)
   JAG_GCASE(32, 1)
@@ -171,6 +181,7 @@ static cudaError_t launch_graph_fmt_plain(const SearchLaunch &L, int P, int CPL)
     case 64: return launch_graph_cap<64, FMT, 0>(L, P, CPL);
     case 128: return launch_graph_cap<128, FMT, 0>(L, P, CPL);
     case 256: return launch_graph_cap<256, FMT, 0>(L, P, CPL);
+    case 512: return launch_graph_cap<512, FMT, 0>(L, P, CPL);
     default: return cudaErrorInvalidValue;
   }
 }

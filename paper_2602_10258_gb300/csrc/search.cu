@@ -471,6 +471,7 @@ int list_capacity(int ls) {
   if (ls <= 64) return 64;
   if (ls <= 128) return 128;
   if (ls <= 256) return 256;
+  if (ls <= 512) return 512;
   return 0;
 }
 

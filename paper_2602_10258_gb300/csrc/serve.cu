@@ -248,6 +248,7 @@ JAG_API jag_status jag_serve_start(jag_index *idx, const jag_serve_params *p, ja
   a.hash_bits = p->hash_bits;
   a.policy = p->policy;
   if (jag_status st = check_search(idx, &a)) return st;
+  if (p->beam > 256) return set_error(JAG_EINVAL, "the serve loop takes beams of at most 256");
   if (p->policy && (p->policy->mode == JAG_POLICY_FORCED || p->policy->forced || p->policy->features ||
                     p->policy->decisions))
     return set_error(JAG_EINVAL, "serving takes a LEARNED or PLAIN policy without per-query buffers");

@@ -60,11 +60,18 @@ class Traces:
     last: np.ndarray       # [nq][nl] last hop that changed the first k entries
     ladder: tuple
 
-    def labels(self, stop_margin=1.5, stop_extra=8, slack=0.0):
-        """(y, t): smallest beam reaching the best recall (minus slack), and the
-        stop target (margin * last change + extra hops) / STOP_SCALE."""
-        best = np.nanmax(np.where(np.isnan(self.recall), -1.0, self.recall), axis=1)
-        ok = self.recall >= (best - slack - 1e-9)[:, None]
+    def labels(self, stop_margin=1.5, stop_extra=8, slack=0.0, target=None):
+        """(y, t): the beam class and the stop target (margin * last change +
+        extra hops) / STOP_SCALE of every query.  The class is the smallest
+        beam whose recall reaches `target` (e.g. 0.95), or, for a query that
+        no beam brings there and when target is None, the smallest beam
+        reaching the best recall over the ladder (minus slack)."""
+        rec = np.where(np.isnan(self.recall), -1.0, self.recall)
+        best = rec.max(axis=1)
+        ok = rec >= (best - slack - 1e-9)[:, None]
+        if target is not None:
+            hit = rec >= target - 1e-9
+            ok = np.where(hit.any(axis=1)[:, None], hit, ok)
         y = np.argmax(ok, axis=1).astype(np.int32)
         last = self.last[np.arange(len(y)), y]
         t = ((stop_margin * last + stop_extra) / STOP_SCALE).astype(np.float32)
@@ -114,3 +121,11 @@ def train(traces: Traces, epochs=60, batch=512, lr=2e-3, lam=0.5, seed=0, device
     tr = jag.Trainer(nl, params)
     trace = tr.run(X, yd, td, epochs=epochs, batch=batch, lr=lr, lam=lam)
     return params, trace
+
+
+def concat_traces(parts):
+    """One Traces of several (for instance those of the two graphs of a
+    mixed workload, searched separately)."""
+    return Traces(np.concatenate([p.X for p in parts]), np.concatenate([p.recall for p in parts]),
+                  np.concatenate([p.cost for p in parts]), np.concatenate([p.hops for p in parts]),
+                  np.concatenate([p.last for p in parts]), parts[0].ladder)

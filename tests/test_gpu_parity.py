@@ -95,7 +95,7 @@ def test_range_small_graph_search(range_small):
 
 
 @pytest.mark.parametrize("k,beam", [(1, 1), (1, 8), (10, 10), (10, 16), (10, 33), (32, 100), (10, 128),
-                                    (64, 200), (256, 256)])
+                                    (64, 200), (256, 256), (10, 300), (10, 512), (256, 512)])
 def test_range_small_beams(range_small, k, beam):
     w, ix, _, gi = range_small
     q, f = w.q[:80], w.filters[:80]
@@ -352,3 +352,17 @@ def test_tensor_core_scan_preselects(case, request):
     if len(big):
         assert (cnt[big, 1] < cnt[big, 2]).mean() > 0.9
         assert cnt[big, 1].mean() < 0.5 * cnt[big, 2].mean()
+
+
+def test_large_beam_rejected_where_unsupported(range_small):
+    """Beams above 256 are for the plain search: a policy or the serve loop
+    rejects them, and a beam above 512 is rejected everywhere."""
+    w, ix, _, gi = range_small
+    q = torch.from_numpy(w.q[:4]).cuda()
+    with pytest.raises(jag.JagError):
+        gi.search(q, w.filters[:4], w.aux, 10, 513, s0=0)
+    pol = jag.Policy(jag.JAG_POLICY_FORCED, h0=4, forced=torch.zeros((4, 2), dtype=torch.int32, device="cuda"))
+    with pytest.raises(jag.JagError):
+        gi.search(q, w.filters[:4], w.aux, 10, 300, s0=0, policy=pol)
+    with pytest.raises(jag.JagError):
+        jag.Server(gi, 10, 300)
