@@ -1073,15 +1073,20 @@ def run_profile(args):
     ground truth): the command profiled by ncu."""
     import torch
     from paper_2602_10258_gb300 import jag
+    from paper_2602_10258_gb300 import datagen as D
     torch.cuda.set_device(0)
-    w = make_workload(args)
+    if args.profile_workload == "subset":
+        w = D.make_subset(n=args.n, d=100, nq=args.nq, seed=args.seed)
+    else:
+        w = make_workload(args)
     idx = jag.Index.from_workload(w, R=R, l_b=LB, alpha=ALPHA, thresholds=THRESHOLDS, storage=args.storage)
     q = torch.from_numpy(w.q).cuda()
     ft = jag.filters_to_device(w.filters, q.device)
     ids = torch.empty((len(w.q), K), dtype=torch.int32, device=q.device)
     dd = torch.empty((len(w.q), K), dtype=torch.float32, device=q.device)
     for _ in range(args.steps):
-        jag.jag_search(idx.h, q, ft, None, K, args.beam, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
+        jag.jag_search(idx.h, q, ft, jag.aux_to_device(w.aux, q.device), K, args.beam, ids, dd, None, None, s0=S0,
+                       scan_cap=SCAN_CAP)
     torch.cuda.synchronize()
     log("profile run done: %d searches of %d queries at beam %d, storage %d" % (args.steps, len(w.q), args.beam,
                                                                                args.storage))
@@ -1117,6 +1122,8 @@ def main():
     ap.add_argument("--large-lb", type=int, default=128, help="build beam of the large form")
     ap.add_argument("--large-alpha", type=float, default=ALPHA, help="pruning alpha of the large form")
     ap.add_argument("--beam", type=int, default=192)
+    ap.add_argument("--profile-workload", default="label", choices=["label", "subset"],
+                    help="workload of the --profile run: the label workload or the precision form's subset one")
     ap.add_argument("--storage", type=int, default=0, help="row storage of the --profile run: 0 fp32, 1 BF16, 2 FP8")
     ap.add_argument("--s0", type=int, default=None, help="scan route threshold (default %d)" % S0)
     ap.add_argument("--scan-cap", type=int, default=None, help="largest scanned set (default %d)" % SCAN_CAP)

@@ -255,7 +255,8 @@ JAG_API jag_status jag_search_host(jag_index *idx, const jag_search_args *args);
  *     (boolean tables) + 512; when s0 > 0: nq * T * (12 * k + 8) bytes
  *     (partial lists and scan work items, T = ceil(max(s0, scan_cap) / 1024))
  *     and, on an index with a mask column, nq * scan_cap * 4 (gathered passing
- *     sets); with JAG_SEARCH_SCAN_ALL: nq * ceil(n / 65536) * 12 * k; on a
+ *     sets) + 12 * H + 8 * nq (grouping of identical filters, H the least
+ *     power of two >= max(64, 2 nq)); with JAG_SEARCH_SCAN_ALL: nq * ceil(n / 65536) * 12 * k; on a
  *     BF16 / FP8 index: nq * min(4k, beam) * 4 (re-ranked ids).  A call that
  *     would need more than 16 MiB returns JAG_EINVAL with the size it needed
  *     in jag_last_error(); split the batch, lower scan_cap, or set s0 = 0.

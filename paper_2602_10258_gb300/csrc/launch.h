@@ -8,15 +8,26 @@
 
 namespace jag {
 
+// Queries of one work item of the tensor-core exact scan at most (the MMA's N).
+constexpr int kTcItemQueries = 64;
+
 // Scratch of the tensor-core exact scan (scan_tc.cu): approximate distances
-// [nq][cap]; per tile of the two sorted columns (2 T0 tiles, T0 = ceil(n /
-// 128)) the count, fill and first entry of its query list; the lists (tq);
-// per work unit (2 T0 tiles, then nq queries) the first work item; block
-// sums of the unit scan.
+// [nq][cap] and |q|^2 [nq]; per work unit (2 T0 tiles of the two sorted
+// columns, T0 = ceil(n / 128), then one list unit per query) the count, fill
+// and first entry of its query list, and its first work item; the lists
+// (tq); the unit of every work item; block sums of the unit scan.
 struct TcScratch {
-  float *approx;
-  int32_t *tcnt, *tfill, *toff, *tq;
+  float *approx, *qnorm;
+  int32_t *tcnt, *tfill, *toff, *tq, *item_unit;
   int64_t *ioff, *bsum;
+};
+
+// Grouping of identical list-routed filters (a hash table of `slots`
+// entries): per query its slot, per slot its leader, and the leaders.
+struct ListGroups {
+  uint64_t *hkey;
+  int32_t *hlead, *lslot, *leaders;
+  size_t slots;
 };
 
 // One jag_search call, resolved to device pointers.
@@ -38,7 +49,8 @@ struct SearchLaunch {
   // scratch
   QueryPlan *plans;
   uint8_t *lut;
-  int32_t *lists;          // [nq][cap] passing ids of list-routed queries
+  int32_t *lists;          // [nq][cap] passing ids gathered by list-routed leaders
+  ListGroups lgroup;       // identical list-routed filters share their leader's list
   int32_t *list_counts;    // [nq]
   unsigned long long *work;  // [4] work counters
   uint32_t *status;
@@ -70,8 +82,9 @@ cudaError_t launch_graph_fmt(const SearchLaunch &L);
 // With tc, the scan route runs on the tensor cores (scan_tc.cu) and its
 // regions replace the fp32 scan's partial lists and work items.
 struct SearchScratch {
-  size_t plans, lut, lists, list_counts, work, status, part_key, part_id, scan_items, rr_ids;
-  size_t approx, tcnt, tfill, toff, tq, ioff, bsum;
+  size_t plans, lut, lists, lhkey, lhlead, lslot, leaders, lslots, list_counts, work, status, part_key, part_id,
+      scan_items, rr_ids;
+  size_t approx, qnorm, tcnt, tfill, toff, tq, item_unit, ioff, bsum;
   size_t total;
   int32_t rr, ntiles, tc;
   int64_t tile;
@@ -98,6 +111,8 @@ cudaError_t run_search(const SearchLaunch &L);
 
 // The tensor-core exact scan of the scan-routed queries (scan_tc.cu).
 cudaError_t launch_scan_tc(const SearchLaunch &L);
+// Slots of a grouping hash table for nq queries: a power of two >= 2 nq.
+size_t tc_slots(int64_t nq);
 // Tiles of 128 positions of a sorted column of n points.
 int64_t tc_column_tiles(int64_t n);
 // |x|^2 of every row into xn and their maximum into *xmax_host (dmax: one

@@ -8,8 +8,9 @@
 //
 //  1. grouping   the sorted columns are cut into tiles of 128 positions;
 //                every slice-routed query is listed at each tile its slice
-//                touches (a counting sort by tile); a gathered subset /
-//                boolean passing set is cut into tiles of its own;
+//                touches (a counting sort by tile); list-routed queries are
+//                listed at their leader (the query that gathered the passing
+//                set of their filter), whose list is cut into tiles of 128;
 //  2. contract   a CTA takes one tile (128 rows) and up to 64 of the queries
 //                listed there, gathers the fp32 rows and queries into shared
 //                memory in the tensor core's K-major layout, and computes all
@@ -48,7 +49,7 @@ namespace jag {
 namespace {
 
 constexpr int kTcRows = 128;         // rows per tile: the MMA's M
-constexpr int kTcQueries = 64;       // queries per tile at most: the MMA's N (padded to 16)
+constexpr int kTcQueries = kTcItemQueries;   // queries per item at most: the MMA's N (padded to 16)
 constexpr int kTcK = 128;            // fp32 elements of a row per pass (K chunk)
 constexpr int kTcThreads = 128;      // four warps: one per 32-lane quarter of tensor memory
 constexpr int kTcCols = 64;          // tensor-memory columns allocated (>= kTcQueries, a power of two >= 32)
@@ -109,37 +110,45 @@ __device__ __forceinline__ bool scan_routed(int32_t route) { return route == kRo
 __device__ __forceinline__ int slice_column(int32_t kind) { return kind == JAG_F_RANGE_F32 ? 1 : 0; }
 
 // Work units of the scan: U = 2 T0 column tiles (T0 = ceil(n / 128) per
-// column), then one unit per query (its gathered list, if list-routed).
+// column), then one unit per query: the list of a leader (the queries that
+// read that leader's gathered list are listed there).
 struct TcUnits {
   int64_t T0, U;
 };
 
-// (1a) each slice-routed query counts itself at every tile its slice touches
-// (one warp per query, lanes over tiles).
-__global__ void tc_count_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, int64_t T0,
+// The unit a scan-routed query is listed at for tile t of its slice, or its
+// leader's list unit.
+__device__ __forceinline__ int64_t list_unit(const TcUnits &tu, const QueryPlan &pl) { return 2 * tu.T0 + pl.begin; }
+
+// (1a) each scan-routed query counts itself at every unit it is listed at
+// (one warp per query, lanes over the tiles of a slice).
+__global__ void tc_count_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, TcUnits tu,
                                 int32_t *tcnt) {
   const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (qi >= nq) return;
   const QueryPlan pl = plans[qi];
+  if (pl.route == kRouteList) {
+    if (lane == 0) atomicAdd(&tcnt[list_unit(tu, pl)], 1);
+    return;
+  }
   if (pl.route != kRouteSlice || pl.end <= pl.begin) return;
-  const int64_t base = slice_column(filters[qi].kind) * T0;
+  const int64_t base = slice_column(filters[qi].kind) * tu.T0;
   for (int64_t t = pl.begin / kTcRows + lane; t <= (pl.end - 1) / kTcRows; t += 32) atomicAdd(&tcnt[base + t], 1);
 }
 
-// Per unit: (query entries of a column tile, work items).  A column tile has
-// one item per chunk of up to 64 listed queries; a list-routed query one
-// item per 128 rows of its list.
+// Per unit: (listed queries, work items).  A column tile has one item per
+// chunk of up to 64 listed queries; a leader's list one per (128 rows of the
+// list, chunk of up to 64 listed queries).
 __device__ __forceinline__ void unit_sizes(int64_t u, const TcUnits &tu, const int32_t *tcnt, const QueryPlan *plans,
                                            int64_t *entries, int64_t *items) {
-  if (u < 2 * tu.T0) {
-    const int64_t c = tcnt[u];
-    *entries = c;
+  const int64_t c = u < tu.U ? tcnt[u] : 0;
+  *entries = c;
+  if (u < 2 * tu.T0 || c == 0) {
     *items = (c + kTcQueries - 1) / kTcQueries;
   } else {
-    const QueryPlan pl = plans[u - 2 * tu.T0];
-    *entries = 0;
-    *items = pl.route == kRouteList ? ((int64_t)pl.count + kTcRows - 1) / kTcRows : 0;
+    const int64_t rows = plans[u - 2 * tu.T0].count;
+    *items = ((rows + kTcRows - 1) / kTcRows) * ((c + kTcQueries - 1) / kTcQueries);
   }
 }
 
@@ -214,25 +223,55 @@ tc_offsets_kernel(TcUnits tu, const int32_t *tcnt, const QueryPlan *plans, const
   const int64_t es = block_scan_incl(e, wsum);
   const int64_t is = block_scan_incl(i, wsum);
   if (u < tu.U) {
-    if (u < 2 * tu.T0) toff[u] = (int32_t)(bsum[2 * blockIdx.x] + es - e);
+    toff[u] = (int32_t)(bsum[2 * blockIdx.x] + es - e);
     ioff[u] = bsum[2 * blockIdx.x + 1] + is - i;
   }
 }
 
-// (1c) each slice-routed query enters the list of every tile its slice
-// touches.
-__global__ void tc_fill_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, int64_t T0,
+// (1c) each scan-routed query enters the list of every unit it counted at.
+__global__ void tc_fill_kernel(const QueryPlan *plans, const jag_filter *filters, int64_t nq, TcUnits tu,
                                const int32_t *toff, int32_t *tfill, int32_t *tq) {
   const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (qi >= nq) return;
   const QueryPlan pl = plans[qi];
+  if (pl.route == kRouteList) {
+    if (lane == 0) {
+      const int64_t u = list_unit(tu, pl);
+      tq[toff[u] + atomicAdd(&tfill[u], 1)] = (int32_t)qi;
+    }
+    return;
+  }
   if (pl.route != kRouteSlice || pl.end <= pl.begin) return;
-  const int64_t base = slice_column(filters[qi].kind) * T0;
+  const int64_t base = slice_column(filters[qi].kind) * tu.T0;
   for (int64_t t = pl.begin / kTcRows + lane; t <= (pl.end - 1) / kTcRows; t += 32) {
     const int32_t pos = atomicAdd(&tfill[base + t], 1);
     tq[toff[base + t] + pos] = (int32_t)qi;
   }
+}
+
+// (1d) the unit of every work item, and |q|^2 of every scan-routed query
+// (one warp per query).
+__global__ void tc_items_kernel(TcUnits tu, const int32_t *tcnt, const QueryPlan *plans, const int64_t *ioff,
+                                int32_t *item_unit) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= tu.U) return;
+  int64_t e, n;
+  unit_sizes(u, tu, tcnt, plans, &e, &n);
+  for (int64_t j = 0; j < n; ++j) item_unit[ioff[u] + j] = (int32_t)u;
+}
+
+__global__ void tc_qnorm_kernel(const QueryPlan *plans, const float *queries, int d, int64_t nq, float *qnorm) {
+  const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (qi >= nq) return;
+  const int32_t r = plans[qi].route;
+  if (r != kRouteSlice && r != kRouteList) return;
+  float acc = 0.f;
+  for (int e = lane; e < d; e += 32) { const float t = queries[qi * d + e]; acc = __fmaf_rn(t, t, acc); }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(kFull, acc, o));
+  if (lane == 0) qnorm[qi] = acc;
 }
 
 // (2) the contraction.  Persistent CTAs of four warps claim work items; per
@@ -244,8 +283,8 @@ __global__ void tc_fill_kernel(const QueryPlan *plans, const jag_filter *filters
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
                    const int32_t *lists, int64_t cap, TcUnits tu, const int32_t *tcnt, const int32_t *toff,
-                   const int32_t *tq, const int64_t *ioff, unsigned long long *counters, float *approx,
-                   uint32_t *status) {
+                   const int32_t *tq, const int64_t *ioff, const int32_t *item_unit, const float *qnorm,
+                   unsigned long long *counters, float *approx, uint32_t *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float *sa = reinterpret_cast<float *>(smem);
@@ -286,12 +325,7 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
     const int64_t item = s_item;
     __syncthreads();   // every thread has read s_item before the next claim overwrites it
     if (item >= (int64_t)ni) break;
-    // the item's unit: the last u with ioff[u] <= item
-    int64_t lo = 0, hi = tu.U - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (ioff[mid] <= item) lo = mid; else hi = mid - 1;
-    }
+    const int64_t lo = item_unit[item];
     const int64_t local = item - ioff[lo];
     int nrow, nqc;
     if (lo < 2 * tu.T0) {
@@ -309,28 +343,29 @@ tc_contract_kernel(DevIndex ix, const float *queries, int d, const jag_filter *f
         s_qid[tid] = qi;
         s_qb[tid] = (int32_t)(t * kTcRows - pl.begin);
         s_qm[tid] = (int32_t)(pl.end - pl.begin);
+        s_qn[tid] = qnorm[qi];
       }
       s_rid[tid] = tid < nrow ? sid[t * kTcRows + tid] : -1;
     } else {
-      // 128 rows of one list-routed query's gathered passing set
-      const int64_t qi = lo - 2 * tu.T0;
-      const int32_t cnt = plans[qi].count;
-      nrow = (int)min64(kTcRows, (int64_t)cnt - local * kTcRows);
-      nqc = 1;
-      if (tid == 0) { s_qid[0] = (int32_t)qi; s_qb[0] = (int32_t)(local * kTcRows); s_qm[0] = cnt; }
-      s_rid[tid] = tid < nrow ? lists[qi * cap + local * kTcRows + tid] : -1;
+      // 128 rows of a leader's gathered list and a chunk of the queries that
+      // share it (row r is position tile * 128 + r of each one's passing set)
+      const int64_t lead = lo - 2 * tu.T0;
+      const int32_t cnt = plans[lead].count;
+      const int64_t nchunk = ((int64_t)tcnt[lo] + kTcQueries - 1) / kTcQueries;
+      const int64_t tile = local / nchunk, chunk = local - tile * nchunk;
+      nrow = (int)min64(kTcRows, (int64_t)cnt - tile * kTcRows);
+      nqc = (int)min64(kTcQueries, (int64_t)tcnt[lo] - chunk * kTcQueries);
+      if (tid < nqc) {
+        const int32_t qi = tq[toff[lo] + chunk * kTcQueries + tid];
+        s_qid[tid] = qi;
+        s_qb[tid] = (int32_t)(tile * kTcRows);
+        s_qm[tid] = cnt;
+        s_qn[tid] = qnorm[qi];
+      }
+      s_rid[tid] = tid < nrow ? lists[lead * cap + tile * kTcRows + tid] : -1;
     }
     const int N = (nqc + 15) & ~15;
     __syncthreads();
-    // |q|^2 of the chunk's queries, one warp per query
-    for (int j = warp; j < nqc; j += kTcThreads / 32) {
-      const float *qr = queries + (int64_t)s_qid[j] * d;
-      float acc = 0.f;
-      for (int e = lane; e < d; e += 32) acc = __fmaf_rn(qr[e], qr[e], acc);
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(kFull, acc, o));
-      if (lane == 0) s_qn[j] = acc;
-    }
     for (int kc = 0; kc < nkc; ++kc) {
       const int k0 = kc * kTcK;
       const int kw = min(kTcK, ((d - k0) + 7) & ~7);   // elements of this chunk, a multiple of 8
@@ -436,7 +471,7 @@ __device__ __forceinline__ void group_rows(const DevIndex &ix, const jag_filter 
     *ids = (slice_column(filters[qi].kind) ? ix.sf32_id : ix.si32_id) + pl.begin;
     *m = pl.end - pl.begin;
   } else {
-    *ids = lists + qi * cap;
+    *ids = lists + pl.begin * cap;   // the leader's list
     *m = pl.count;
   }
 }
@@ -589,20 +624,22 @@ cudaError_t launch_scan_tc(const SearchLaunch &L) {
   tu.T0 = tc_column_tiles(L.ix.n);
   tu.U = 2 * tu.T0 + nq;
   const int64_t nblk = (tu.U + kTcScanBlock - 1) / kTcScanBlock;
-  if ((e = cudaMemsetAsync(T.tcnt, 0, sizeof(int32_t) * 2 * (size_t)tu.T0, L.stream)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(T.tfill, 0, sizeof(int32_t) * 2 * (size_t)tu.T0, L.stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(T.tcnt, 0, sizeof(int32_t) * (size_t)tu.U, L.stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(T.tfill, 0, sizeof(int32_t) * (size_t)tu.U, L.stream)) != cudaSuccess) return e;
   const unsigned wb = (unsigned)((nq * 32 + 255) / 256);   // one warp per query
-  tc_count_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.filters, nq, tu.T0, T.tcnt);
+  tc_count_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.filters, nq, tu, T.tcnt);
   tc_sum_kernel<<<(unsigned)nblk, kTcScanBlock, 0, L.stream>>>(tu, T.tcnt, L.plans, T.bsum);
   tc_sum_blocks_kernel<<<1, kTcScanBlock, 0, L.stream>>>(nblk, T.bsum, L.work + 4);
   tc_offsets_kernel<<<(unsigned)nblk, kTcScanBlock, 0, L.stream>>>(tu, T.tcnt, L.plans, T.bsum, T.toff, T.ioff);
-  tc_fill_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.filters, nq, tu.T0, T.toff, T.tfill, T.tq);
+  tc_fill_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.filters, nq, tu, T.toff, T.tfill, T.tq);
+  tc_items_kernel<<<(unsigned)((tu.U + 255) / 256), 256, 0, L.stream>>>(tu, T.tcnt, L.plans, T.ioff, T.item_unit);
+  tc_qnorm_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.queries, L.d, nq, T.qnorm);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int bps = blocks_per_sm(tc_contract_kernel, kTcSmem, kTcThreads / 32);
   if (bps == 0) return cudaErrorInvalidConfiguration;
   tc_contract_kernel<<<(unsigned)(bps * num_sms()), kTcThreads, kTcSmem, L.stream>>>(
-      L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, tu, T.tcnt, T.toff, T.tq, T.ioff, L.work + 4,
-      T.approx, L.status);
+      L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, tu, T.tcnt, T.toff, T.tq, T.ioff, T.item_unit,
+      T.qnorm, L.work + 4, T.approx, L.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int P, CPL;
   if (!row_mapping(L.ix.nchunks, &P, &CPL)) return cudaErrorInvalidValue;

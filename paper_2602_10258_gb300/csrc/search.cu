@@ -54,29 +54,84 @@ prep_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, int64_t 
   }
 }
 
+// Exact key of a list-routed filter, shared by identical filters: a subset
+// filter's required bits (below bit 62), or a boolean filter over m <= 4 bits
+// as its m, bit positions and truth table.  false: no shareable key (the
+// query gathers a list of its own).
+__device__ __forceinline__ bool list_key(const jag_filter &f, const uint8_t *aux, uint64_t *key) {
+  if (f.kind == JAG_F_SUBSET) {
+    if (f.payload >> 62) return false;
+    *key = (1ull << 62) | f.payload;
+    return true;
+  }
+  if (f.kind != JAG_F_BOOL) return false;
+  const int m = __popcll(f.payload);
+  if (m > 4) return false;
+  uint64_t pos = 0;
+  int j = 0;
+  for (uint64_t v = f.payload; v; v &= v - 1, ++j) pos |= (uint64_t)(__ffsll((long long)v) - 1) << (6 * j);
+  uint64_t t = aux[f.aux_off];
+  if (m == 4) t |= (uint64_t)aux[f.aux_off + 1] << 8;
+  if (m < 3) t &= (1ull << (1 << m)) - 1;   // the 2^m bits of the table
+  *key = (1ull << 63) | ((uint64_t)m << 56) | (t << 24) | pos;
+  return true;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t v) {
+  v ^= v >> 33; v *= 0xFF51AFD7ED558CCDull; v ^= v >> 33; v *= 0xC4CEB9FE1A85EC53ull; v ^= v >> 33;
+  return v;
+}
+
+// K1a: list-routed queries with the same filter join one hash slot; the
+// slot's leader is its lowest query index (lslot[qi] = slot, -1 if the
+// filter has no shareable key).
+__global__ void list_group_kernel(const QueryPlan *plans, const jag_filter *filters, const uint8_t *aux, int64_t nq,
+                                  uint64_t *hkey, int32_t *hlead, uint32_t hmask, int32_t *lslot) {
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= nq) return;
+  if (plans[qi].route != kRouteList) return;
+  uint64_t key;
+  if (!list_key(filters[qi], aux, &key)) { lslot[qi] = -1; return; }
+  uint32_t h = (uint32_t)mix64(key) & hmask;
+  for (uint32_t probe = 0; probe <= hmask; ++probe) {   // at least 2 nq slots
+    const unsigned long long old = atomicCAS((unsigned long long *)&hkey[h], ~0ull, (unsigned long long)key);
+    if (old == ~0ull || old == key) break;
+    h = (h + 1) & hmask;
+  }
+  atomicMin(&hlead[h], (int32_t)qi);
+  lslot[qi] = (int32_t)h;
+}
+
+// K1b: every list-routed query records its leader in plan.begin (the query
+// whose gathered list it reads); leaders are listed for the gather.
+__global__ void list_leader_kernel(QueryPlan *plans, int64_t nq, const int32_t *hlead, const int32_t *lslot,
+                                   int32_t *leaders, unsigned long long *nlead) {
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= nq) return;
+  if (plans[qi].route != kRouteList) return;
+  const int32_t s = lslot[qi];
+  const int64_t lead = s < 0 ? qi : hlead[s];
+  plans[qi].begin = lead;
+  if (lead == qi) leaders[atomicAdd(nlead, 1ull)] = (int32_t)qi;
+}
+
 // K2: one pass over a tile of masks evaluates the predicates of up to
-// kGatherQPB list-routed queries and appends the passing ids.
+// kGatherQPB leaders and appends the passing ids to their lists.
 __global__ void __launch_bounds__(256)
-gather_list_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, const QueryPlan *plans,
-                   int64_t nq, int64_t cap, int32_t *lists, int32_t *counts) {
+gather_list_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, const int32_t *leaders,
+                   const unsigned long long *nlead, int64_t cap, int32_t *lists, int32_t *counts) {
   __shared__ uint64_t sm[kGatherTile];
   const int64_t t0 = (int64_t)blockIdx.x * kGatherTile;
   const int64_t t1 = min64(ix.n, t0 + kGatherTile);
   const int64_t q0 = (int64_t)blockIdx.y * kGatherQPB;
-  // skip the tile load when no query of this group is list-routed
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
-  __syncthreads();
-  if (threadIdx.x < kGatherQPB && q0 + threadIdx.x < nq && plans[q0 + threadIdx.x].route == kRouteList) any = 1;
-  __syncthreads();
-  if (!any) return;
+  const int64_t nl = (int64_t)*nlead;
+  if (q0 >= nl) return;
   for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) sm[i - t0] = ix.a_mask[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int qq = warp; qq < kGatherQPB; qq += nw) {
-    const int64_t qi = q0 + qq;
-    if (qi >= nq) break;
-    if (plans[qi].route != kRouteList) continue;
+    if (q0 + qq >= nl) break;
+    const int64_t qi = leaders[q0 + qq];
     const jag_filter f = filters[qi];
     const uint8_t *tt = f.kind == JAG_F_BOOL ? aux + f.aux_off : nullptr;
     for (int64_t b = t0; b < t1; b += 32) {
@@ -100,13 +155,13 @@ gather_list_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, c
   }
 }
 
-// A list-routed query whose passing set exceeds the scan capacity goes back
-// to the graph search.
+// A list-routed query takes its leader's passing count; one whose passing
+// set exceeds the scan capacity goes back to the graph search.
 __global__ void finalize_routes_kernel(QueryPlan *plans, const int32_t *counts, int64_t nq, int64_t cap) {
   const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= nq) return;
   if (plans[qi].route != kRouteList) return;
-  const int32_t c = counts[qi];
+  const int32_t c = counts[plans[qi].begin];
   plans[qi].count = c;
   if (c > cap) plans[qi].route = kRouteGraph;
 }
@@ -170,7 +225,7 @@ __device__ __forceinline__ void routed_candidates(const DevIndex &ix, const jag_
     *ids = (kind == JAG_F_RANGE_F32 ? ix.sf32_id : ix.si32_id) + pl.begin;
     *m = pl.end - pl.begin;
   } else {
-    *ids = lists + qi * cap;
+    *ids = lists + pl.begin * cap;   // the list of the query's leader (the same filter)
     *m = pl.count;
   }
 }
@@ -467,6 +522,12 @@ cudaError_t build_edge_attrs(const DevIndex &ix, int32_t *ea_i32, float *ea_f32,
 // host side
 // ---------------------------------------------------------------------------
 
+size_t tc_slots(int64_t nq) {
+  size_t h = 64;
+  while (h < (size_t)std::max<int64_t>(nq, 1) * 2) h <<= 1;
+  return h;
+}
+
 int list_capacity(int ls) {
   if (ls <= 64) return 64;
   if (ls <= 128) return 128;
@@ -519,12 +580,17 @@ SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_
   // a slice of at most cap rows touches at most cap / 128 + 2 tiles; the
   // tile lists are indexed with int32, else the fp32 scan kernels run
   const size_t tc_entries = q1 * ((size_t)cap / 128 + 2);
-  if (tc_entries >= ((size_t)1 << 31)) s.tc = 0;
+  if (tc_entries + q1 >= ((size_t)1 << 31)) s.tc = 0;
   const bool parts_needed = scan_all || (s0 > 0 && !s.tc);
   size_t off = 0;
   s.plans = off; off += align256(sizeof(QueryPlan) * q1);
   s.lut = off; off += align256((size_t)std::max<int64_t>(aux_bytes, 1) * 8);
   s.lists = off; off += lists ? align256(q1 * (size_t)cap * 4) : 256;
+  s.lslots = lists ? tc_slots(nq) : 1;
+  s.lhkey = off; off += align256(s.lslots * 8);
+  s.lhlead = off; off += align256(s.lslots * 4);
+  s.lslot = off; off += align256((lists ? q1 : 1) * 4);
+  s.leaders = off; off += align256((lists ? q1 : 1) * 4);
   s.list_counts = off; off += align256(q1 * 4);
   s.work = off; off += 256;
   s.status = off; off += 256;
@@ -536,11 +602,16 @@ SearchScratch search_scratch_layout(const DevIndex &ix, int64_t nq, int64_t aux_
   s.rr_ids = off; off += align256(q1 * (size_t)std::max(s.rr, 1) * 4);
   if (s.tc) {
     const size_t T0 = (size_t)tc_column_tiles(ix.n), U = 2 * T0 + q1;
+    // work items: column tiles at most 2 T0 + (entries) / 64; leaders' lists
+    // at most (cap / 128 + 1) per listed query and one more per leader
+    const size_t items = 2 * T0 + tc_entries / kTcItemQueries + 2 * q1 * ((size_t)cap / 128 + 1);
     s.approx = off; off += align256(q1 * (size_t)cap * 4);
-    s.tcnt = off; off += align256(2 * T0 * 4);
-    s.tfill = off; off += align256(2 * T0 * 4);
-    s.toff = off; off += align256(2 * T0 * 4);
-    s.tq = off; off += align256(tc_entries * 4);
+    s.qnorm = off; off += align256(q1 * 4);
+    s.tcnt = off; off += align256(U * 4);
+    s.tfill = off; off += align256(U * 4);
+    s.toff = off; off += align256(U * 4);
+    s.tq = off; off += align256((tc_entries + q1) * 4);
+    s.item_unit = off; off += align256(items * 4);
     s.ioff = off; off += align256(U * 8);
     s.bsum = off; off += align256(((U + 1023) / 1024) * 16);
   }
@@ -552,6 +623,11 @@ void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base) {
   L.plans = reinterpret_cast<QueryPlan *>(base + s.plans);
   L.lut = base + s.lut;
   L.lists = reinterpret_cast<int32_t *>(base + s.lists);
+  L.lgroup.hkey = reinterpret_cast<uint64_t *>(base + s.lhkey);
+  L.lgroup.hlead = reinterpret_cast<int32_t *>(base + s.lhlead);
+  L.lgroup.lslot = reinterpret_cast<int32_t *>(base + s.lslot);
+  L.lgroup.leaders = reinterpret_cast<int32_t *>(base + s.leaders);
+  L.lgroup.slots = s.lslots;
   L.list_counts = reinterpret_cast<int32_t *>(base + s.list_counts);
   L.work = reinterpret_cast<unsigned long long *>(base + s.work);
   L.status = reinterpret_cast<uint32_t *>(base + s.status);
@@ -565,6 +641,8 @@ void bind_scratch(SearchLaunch &L, const SearchScratch &s, uint8_t *base) {
   L.tc = TcScratch{};
   if (s.tc) {
     L.tc.approx = reinterpret_cast<float *>(base + s.approx);
+    L.tc.qnorm = reinterpret_cast<float *>(base + s.qnorm);
+    L.tc.item_unit = reinterpret_cast<int32_t *>(base + s.item_unit);
     L.tc.tcnt = reinterpret_cast<int32_t *>(base + s.tcnt);
     L.tc.tfill = reinterpret_cast<int32_t *>(base + s.tfill);
     L.tc.toff = reinterpret_cast<int32_t *>(base + s.toff);
@@ -684,9 +762,17 @@ cudaError_t run_search(const SearchLaunch &L) {
   }
   if (L.scan_all) return dispatch_job(L, P, CPL, kJobBrute, L.k);
   if (L.s0 > 0 && L.ix.a_mask) {
+    // identical list-routed filters share one gathered list (their leader's)
+    const unsigned qb = (unsigned)((L.nq + 255) / 256);
+    if ((e = cudaMemsetAsync(L.lgroup.hkey, 0xFF, L.lgroup.slots * 8, L.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(L.lgroup.hlead, 0x7F, L.lgroup.slots * 4, L.stream)) != cudaSuccess) return e;
+    list_group_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.filters, L.aux, L.nq, L.lgroup.hkey, L.lgroup.hlead,
+                                                (uint32_t)(L.lgroup.slots - 1), L.lgroup.lslot);
+    list_leader_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.nq, L.lgroup.hlead, L.lgroup.lslot, L.lgroup.leaders,
+                                                 L.work + 8);
     dim3 grid((unsigned)((L.ix.n + kGatherTile - 1) / kGatherTile), (unsigned)((L.nq + kGatherQPB - 1) / kGatherQPB));
-    gather_list_kernel<<<grid, 256, 0, L.stream>>>(L.ix, L.filters, L.aux, L.plans, L.nq, L.cap, L.lists,
-                                                   L.list_counts);
+    gather_list_kernel<<<grid, 256, 0, L.stream>>>(L.ix, L.filters, L.aux, L.lgroup.leaders, L.work + 8, L.cap,
+                                                   L.lists, L.list_counts);
     finalize_routes_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.plans, L.list_counts, L.nq,
                                                                                  L.cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

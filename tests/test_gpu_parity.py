@@ -289,7 +289,7 @@ def test_invalid_filter_reported_by_host_call(range_small):
 def test_argument_errors(range_small):
     w, ix, _, gi = range_small
     q = torch.from_numpy(w.q[:4]).cuda()
-    for k, beam in ((11, 10), (0, 10), (1, 257)):
+    for k, beam in ((11, 10), (0, 10), (1, 513), (257, 300)):
         with pytest.raises(jag.JagError) as e:
             gi.search(q, w.filters[:4], w.aux, k, beam)
         assert e.value.status == jag.JAG_EINVAL
