@@ -361,6 +361,12 @@ def run_ours(args):
     mixed = None
     if not args.no_mixed:
         mixed = measure_mixed(args, local, flush, stream)
+    subset = None
+    if not args.no_subset:
+        subset = measure_subset(args, local, flush, stream)
+    large = None
+    if not args.no_large:
+        large = measure_large(args, local)
 
     cpu, ocnt = None, None
     if rank == 0 and not args.no_cpu:
@@ -409,6 +415,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "forms": forms,
         "learned_form_mixed": mixed,
+        "precision_form_subset": subset,
+        "serving_form_10m": large,
         "serving": serving,
         "clocks": clk.summary(),
         # per step: prep, graph search, scan work items, scan tiles, scan merge
@@ -821,6 +829,114 @@ def measure_mixed(args, local, flush, stream):
     return out
 
 
+# ---------------------------------------------------------------------------
+# the precision form's workload: subset filters over 64-bit label masks
+# ---------------------------------------------------------------------------
+
+SUBSET_R = 64
+SUBSET_WEIGHTS = (0, 1, 5)      # Weight-JAG multipliers of the mask graph (Hamming dist_A)
+SUBSET_BEAMS = (64, 96, 128, 160, 192, 256, 320, 384, 512)
+
+
+def subset_selectivity(w, dev):
+    """Exact selectivity of every subset filter (torch on the GPU; bookkeeping)."""
+    import torch
+    mt = torch.from_numpy(w.attr_mask.view(np.int64)).to(dev)
+    req = w.filters["payload"].view(np.int64)
+    sel = np.zeros(len(req))
+    for i0 in range(0, len(req), 64):
+        r = torch.from_numpy(np.ascontiguousarray(req[i0:i0 + 64])).to(dev)
+        sel[i0:i0 + 64] = ((mt[None, :] & r[:, None]) == r[:, None]).sum(1).cpu().numpy() / w.n
+    return sel
+
+
+def measure_subset(args, local, flush, stream):
+    """The precision form: N = 1M, d = 100 (200-component mixture), a 64-bit
+    label mask per point (bit j with probability 0.5/(j+1)), 10,000 subset
+    queries requiring 1-3 labels; rows stored as fp32, BF16 and FP8-E4M3 with
+    a per-row scale (fp32 re-rank of the leading min(4k, beam) candidates).
+    Per format: the smallest beam with recall@10 >= 0.95 in every band, its
+    QPS, and the stored distance's error against fp64."""
+    import torch
+    from paper_2602_10258_gb300 import datagen as D
+    from paper_2602_10258_gb300 import jag
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    w = D.make_subset(n=args.n, d=100, nq=args.nq, seed=args.seed)
+    sel = subset_selectivity(w, dev)
+    band = band_of(sel)
+    ix32 = jag.Index.from_workload(w, R=SUBSET_R, l_b=64, alpha=ALPHA, weights=SUBSET_WEIGHTS, device=local)
+    info = ix32.info()
+    graph, entry = ix32.graph(), info["entry"]
+    prep_s = time.time() - t0
+    nq = len(w.q)
+    q = torch.from_numpy(w.q).to(dev)
+    ft = jag.filters_to_device(w.filters, dev)
+    at = jag.aux_to_device(w.aux, dev)
+    gt_ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    gt_d = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    jag.jag_search(ix32.h, q, ft, at, K, K, gt_ids, gt_d, None, stream, flags=jag.JAG_SEARCH_SCAN_ALL)
+    torch.cuda.synchronize()
+    gt_ids, gt_d = gt_ids.cpu().numpy(), gt_d.cpu().numpy()
+    out = {"workload": "subset filter, 64-bit masks with P(bit j) = 0.5/(j+1), 1-3 required labels "
+                       "(selectivity 1e-4..0.5), N=%d d=100 fp32 GMM-200, %d queries, k=10" % (w.n, nq),
+           "graph": "Weight-JAG R=%d, weights %s (Hamming dist_A), l_b=64, GPU build %.2f s"
+                    % (SUBSET_R, list(SUBSET_WEIGHTS), info["build_seconds"]),
+           "band_queries": {name: int((band == j).sum()) for j, (_, _, name) in enumerate(BANDS)},
+           "prep_seconds": round(time.time() - t0, 1)}
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev)
+    steps = min(args.steps, 50)
+    forms = {}
+    for fname, fcode in (("fp32", jag.JAG_VEC_F32), ("bf16", jag.JAG_VEC_BF16), ("fp8", jag.JAG_VEC_FP8)):
+        gi = ix32 if fcode == jag.JAG_VEC_F32 else jag.Index.from_workload(w, R=SUBSET_R, graph=graph, entry=entry,
+                                                                            storage=fcode, device=local)
+        chosen, per = None, None
+        for beam in SUBSET_BEAMS:
+            jag.jag_search(gi.h, q, ft, at, K, beam, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
+            torch.cuda.synchronize()
+            per = band_recalls(recall_at_k(ids.cpu().numpy(), gt_ids), band)
+            if all(v >= 0.95 for v in per.values()):
+                chosen = beam
+                break
+        met = chosen is not None
+        chosen = chosen or SUBSET_BEAMS[-1]
+        jag.jag_search(gi.h, q, ft, at, K, chosen, ids, dd, cnt, stream, s0=S0, scan_cap=SCAN_CAP)
+        torch.cuda.synchronize()
+        c = cnt.cpu().numpy()
+        for _ in range(3):
+            jag.jag_search(gi.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
+        evs = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b, ka, kb = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            ka.record(stream)
+            kb.record(stream)
+            a.record(stream)
+            jag.jag_search(gi.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP, ev_begin=ka,
+                           ev_end=kb)
+            b.record(stream)
+            evs.append((a, b, ka, kb))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b, _, _ in evs]))
+        kms = float(np.mean([ka.elapsed_time(kb) for _, _, ka, kb in evs]))
+        row_bytes = 400 if fcode == jag.JAG_VEC_F32 else (208 if fcode == jag.JAG_VEC_BF16 else 116)
+        gbytes = mixed_graph_bytes(c, row_bytes, 8, SUBSET_R)
+        forms[fname] = {"beam": chosen, "recall_0.95_met": met, "qps": round(nq / (ms / 1e3), 1),
+                        "ms_per_step": round(ms, 4), "graph_kernel_ms": round(kms, 3), "recall": per,
+                        "routed_to_scan": int((c[:, 3] == 1).sum()),
+                        "graph_kernel_gather_bytes": gbytes,
+                        "graph_kernel_frac_of_hbm": round(gbytes / (kms / 1e3) / 1e9 / measured_peaks()[0], 4)}
+        if fcode != jag.JAG_VEC_F32:
+            forms[fname]["distance_error_vs_fp64"] = stored_distance_error(gi, w, gt_ids, fcode)
+            gi.close()
+        log("subset %s: beam %d, %.0f QPS, %s" % (fname, chosen, nq / (ms / 1e3), per))
+    ix32.close()
+    out["forms"] = forms
+    return out
+
+
 def serve_saturation(jag, idx, w, beam, batch_qps, n_req=2000, offered=(0.6, 0.8, 1.0)):
     """Saturated throughput of the serve loop: the largest QPS it achieves
     under Poisson arrivals of the request mix (sizes uniform in 1..256
@@ -979,25 +1095,31 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+LARGE_BEAMS = (128, 192, 256, 320, 384, 448, 512)
+
+
 def run_serve_large(args):
+    print(json.dumps(measure_large(args, 0)))
+
+
+def measure_large(args, local):
     """The serving form at its own scale: N = 10M, d = 100, BF16 rows (fp32
     re-rank), float attribute U[0,1), range filters of width log-uniform in
-    [1e-4, 1].  Picks the smallest beam with recall@10 >= 0.95 in every band
-    on a ground-truth sample (else the largest beam, and says so), times the
-    batch search, then replays Poisson traffic at 0.5x and 0.8x of that
-    throughput through the serve loop.  Prints one JSON line."""
+    [1e-4, 1], R = 32.  Picks the smallest beam with recall@10 >= 0.95 in
+    every band on a ground-truth sample (else the largest beam, and says so),
+    times the batch search at that beam and at 256 (the serve loop's largest),
+    then replays Poisson traffic through the serve loop at beam <= 256."""
     import torch
     from paper_2602_10258_gb300 import datagen as D
     from paper_2602_10258_gb300 import jag
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local)
     t0 = time.time()
     w = D.make_range_f32(n=args.large_n, d=100, nq=10000, seed=args.seed)
     gen_s = time.time() - t0
     t0 = time.time()
     thr = tuple(int(v) for v in args.large_thresholds.split(","))
     idx = jag.Index.from_workload(w, R=R, l_b=args.large_lb, alpha=args.large_alpha, thresholds=thr,
-                                  storage=jag.JAG_VEC_BF16)
+                                  storage=jag.JAG_VEC_BF16, device=local)
     build_s = time.time() - t0
     info = idx.info()
     log("large: data %.1f s, build %.1f s (GPU %.1f s), %.2f GB on the device" % (
@@ -1021,7 +1143,7 @@ def run_serve_large(args):
     ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
     dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
     chosen, per_chosen, sweep, per = None, None, {}, {}
-    for beam in BEAMS:
+    for beam in LARGE_BEAMS:
         jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
         torch.cuda.synchronize()
         rec = recall_at_k(ids.cpu().numpy()[:ns], gt, gd)
@@ -1034,26 +1156,34 @@ def run_serve_large(args):
             break
     met = chosen is not None
     if not met:
-        chosen, per_chosen = BEAMS[-1], per
+        chosen, per_chosen = LARGE_BEAMS[-1], per
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(3):
-        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
-    evs = []
-    for i in range(min(args.steps, 20)):
-        flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
-        b.record()
-        evs.append((a, b))
-    torch.cuda.synchronize()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    def batch_ms(beam):
+        for _ in range(3):
+            jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
+        evs = []
+        for i in range(min(args.steps, 20)):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            jag.jag_search(idx.h, q, ft, at, K, beam, ids, dd, None, None, s0=S0, scan_cap=SCAN_CAP)
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    ms = batch_ms(chosen)
     qps = nq / (ms / 1000.0)
+    serve_beam = min(chosen, 256)
+    ms_serve_beam = batch_ms(serve_beam) if serve_beam != chosen else ms
     gt_all = np.concatenate([gt, np.full((nq - ns, K), -1, np.int32)])
     gd_all = np.concatenate([gd, np.full((nq - ns, K), np.inf, np.float32)])
-    serving = measure_serving(jag, idx, w, chosen, band, gt_all, gd_all, qps)
+    serving = measure_serving(jag, idx, w, serve_beam, band, gt_all, gd_all, nq / (ms_serve_beam / 1000.0))
+    serving["beam"] = serve_beam
+    serving["recall_at_beam"] = sweep.get(serve_beam)
     idx.close()
-    out = {"mode": "serve_large", "metric": METRIC, "unit": "queries/s", "dtype": "bf16 rows, f32 re-rank",
+    out = {"metric": METRIC, "unit": "queries/s", "dtype": "bf16 rows, f32 re-rank",
            "data": "synthetic",
            "config": {"workload": "float range, width log-uniform 1e-4..1, N=%d d=100 GMM-200, 10000 queries, "
                                   "k=10, R=%d" % (w.n, R), "beam": chosen, "recall_0.95_met": met, "s0": S0,
@@ -1063,9 +1193,10 @@ def run_serve_large(args):
                       "build_seconds": round(build_s, 1), "gpu_build_seconds": round(info["build_seconds"], 1),
                       "index_device_bytes": info["device_bytes"], "ground_truth_sample": ns,
                       "ground_truth_seconds": round(gt_s, 1), "beam_sweep": {str(b): v for b, v in sweep.items()}},
-           "batch": {"qps": round(qps, 1), "ms_per_step": round(ms, 3), "recall": per_chosen},
+           "batch": {"qps": round(qps, 1), "ms_per_step": round(ms, 3), "recall": per_chosen,
+                     "beam_256_qps": round(nq / (ms_serve_beam / 1000.0), 1)},
            "serving": serving}
-    print(json.dumps(out))
+    return out
 
 
 def run_profile(args):
@@ -1108,6 +1239,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the learned form's mixed range / boolean workload")
+    ap.add_argument("--no-subset", action="store_true", help="skip the precision form's subset workload")
+    ap.add_argument("--subset-only", action="store_true", help="only the precision form's subset workload")
     ap.add_argument("--mixed-train", type=int, default=100_000, help="training queries of the learned form")
     ap.add_argument("--mixed-epochs", type=int, default=40)
     ap.add_argument("--mixed-only", action="store_true", help="only the mixed workload's forms (prints its JSON)")
@@ -1115,7 +1248,8 @@ def main():
     ap.add_argument("--ref-beam", type=int, default=192)
     ap.add_argument("--ref-queries", type=int, default=200)
     ap.add_argument("--profile", action="store_true", help="fixed-beam searches only (for ncu)")
-    ap.add_argument("--serve-large", action="store_true", help="the 10M BF16 serving form (not in the default run)")
+    ap.add_argument("--serve-large", action="store_true", help="only the 10M BF16 serving form")
+    ap.add_argument("--no-large", action="store_true", help="skip the 10M BF16 serving form")
     ap.add_argument("--large-n", type=int, default=10_000_000)
     ap.add_argument("--large-gt", type=int, default=2000, help="queries with ground truth in the large form")
     ap.add_argument("--large-thresholds", default="100,10,0", help="threshold percentiles of the large form's build")
@@ -1134,7 +1268,12 @@ def main():
         SCAN_CAP = args.scan_cap
     if args.warmup < 3:
         args.warmup = 3
-    if args.mixed_only:
+    if args.subset_only:
+        import torch
+        torch.cuda.set_device(0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(measure_subset(args, 0, flush, torch.cuda.current_stream())))
+    elif args.mixed_only:
         import torch
         torch.cuda.set_device(0)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

@@ -326,6 +326,23 @@ jag_status jag_build(const jag_build_params *p, jag_index **out) {
     API_TRY(I->alloc((void **)&a, 8 * (size_t)n), "allocate attr_mask");
     API_TRY(cudaMemcpy(a, p->attr_mask, 8 * (size_t)n, cudaMemcpyHostToDevice), "copy attr_mask");
     ix.a_mask = a;
+    // posting lists per bit (CSR), for the exact scan of subset filters
+    std::vector<int64_t> off(65, 0);
+    for (int64_t i = 0; i < n; ++i)
+      for (uint64_t v = p->attr_mask[i]; v; v &= v - 1) off[__builtin_ctzll(v) + 1] += 1;
+    for (int j = 0; j < 64; ++j) off[j + 1] += off[j];
+    std::vector<int32_t> ids((size_t)std::max<int64_t>(off[64], 1));
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (uint64_t v = p->attr_mask[i]; v; v &= v - 1) ids[(size_t)fill[__builtin_ctzll(v)]++] = (int32_t)i;
+    int64_t *doff;
+    int32_t *dids;
+    API_TRY(I->alloc((void **)&doff, sizeof(int64_t) * 65), "allocate posting lists");
+    API_TRY(I->alloc((void **)&dids, sizeof(int32_t) * ids.size()), "allocate posting lists");
+    API_TRY(cudaMemcpy(doff, off.data(), sizeof(int64_t) * 65, cudaMemcpyHostToDevice), "copy posting lists");
+    API_TRY(cudaMemcpy(dids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice), "copy posting lists");
+    ix.bit_off = doff;
+    ix.bit_ids = dids;
   }
   API_TRY(I->alloc((void **)&I->graph, sizeof(int32_t) * (size_t)(n * p->R)), "allocate graph");
   ix.graph = I->graph;

@@ -69,6 +69,10 @@ struct DevIndex {
   const float *xnorm;
   float xnorm_max;
   int32_t pad2;
+  // posting lists of the mask column: the ids of the points with bit j set
+  // are bit_ids[bit_off[j] .. bit_off[j + 1]), in increasing order
+  const int64_t *bit_off;
+  const int32_t *bit_ids;
 };
 
 // Elements of one 16-byte chunk of a stored row, per format.

@@ -103,35 +103,97 @@ __global__ void list_group_kernel(const QueryPlan *plans, const jag_filter *filt
 }
 
 // K1b: every list-routed query records its leader in plan.begin (the query
-// whose gathered list it reads); leaders are listed for the gather.
-__global__ void list_leader_kernel(QueryPlan *plans, int64_t nq, const int32_t *hlead, const int32_t *lslot,
-                                   int32_t *leaders, unsigned long long *nlead) {
+// whose gathered list it reads); leaders are listed for the gather: subset
+// filters with a required bit (gathered from a posting list) from the front
+// of `leaders`, the others (a pass over the mask column) from the back.
+__global__ void list_leader_kernel(QueryPlan *plans, const jag_filter *filters, int64_t nq, const int32_t *hlead,
+                                   const int32_t *lslot, int32_t *leaders, unsigned long long *nlead) {
   const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= nq) return;
   if (plans[qi].route != kRouteList) return;
   const int32_t s = lslot[qi];
   const int64_t lead = s < 0 ? qi : hlead[s];
   plans[qi].begin = lead;
-  if (lead == qi) leaders[atomicAdd(nlead, 1ull)] = (int32_t)qi;
+  if (lead != qi) return;
+  const jag_filter f = filters[qi];
+  if (f.kind == JAG_F_SUBSET && f.payload != 0) leaders[atomicAdd(&nlead[0], 1ull)] = (int32_t)qi;
+  else leaders[nq - 1 - (int64_t)atomicAdd(&nlead[1], 1ull)] = (int32_t)qi;
 }
 
-// K2: one pass over a tile of masks evaluates the predicates of up to
-// kGatherQPB leaders and appends the passing ids to their lists.
+// K2a: one CTA per subset leader walks the posting list of its rarest
+// required bit and keeps the points that hold every required bit; each lane
+// keeps kPostUnroll loads in flight.  Past cap points the list is full and
+// the count only has to exceed cap (the query then goes to the graph).
+constexpr int kPostWarps = 8;
+constexpr int kPostUnroll = 4;
+
+__global__ void __launch_bounds__(kPostWarps * 32)
+gather_postings_kernel(DevIndex ix, const jag_filter *filters, const int32_t *leaders,
+                       const unsigned long long *nlead, int64_t cap, int32_t *lists, int32_t *counts) {
+  __shared__ int s_cnt;
+  const int64_t w = blockIdx.x;
+  if (w >= (int64_t)nlead[0]) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t qi = leaders[w];
+  const uint64_t f = filters[qi].payload;
+  int jb = 0;
+  int64_t best = INT64_MAX;
+  for (uint64_t v = f; v; v &= v - 1) {
+    const int j = __ffsll((long long)v) - 1;
+    const int64_t len = ix.bit_off[j + 1] - ix.bit_off[j];
+    if (len < best) { best = len; jb = j; }
+  }
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  const int64_t b0 = ix.bit_off[jb], b1 = ix.bit_off[jb + 1];
+  constexpr int kStep = kPostWarps * 32 * kPostUnroll;
+  for (int64_t b = b0 + (threadIdx.x >> 5) * 32 * kPostUnroll; b < b1; b += kStep) {
+    if (*(volatile int *)&s_cnt > cap) break;   // full: the count is already past cap
+    int32_t u[kPostUnroll];
+    uint64_t a[kPostUnroll];
+#pragma unroll
+    for (int r = 0; r < kPostUnroll; ++r) {
+      const int64_t e = b + r * 32 + lane;
+      u[r] = e < b1 ? ix.bit_ids[e] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < kPostUnroll; ++r) a[r] = u[r] >= 0 ? ix.a_mask[u[r]] : 0ull;
+#pragma unroll
+    for (int r = 0; r < kPostUnroll; ++r) {
+      const bool pass = u[r] >= 0 && (a[r] & f) == f;
+      const uint32_t m = __ballot_sync(kFull, pass);
+      if (!m) continue;
+      int off = 0;
+      if (lane == 0) off = atomicAdd(&s_cnt, __popc(m));
+      off = __shfl_sync(kFull, off, 0);
+      if (pass) {
+        const int64_t pos = off + __popc(m & lanemask_lt());
+        if (pos < cap) lists[qi * cap + pos] = u[r];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) counts[qi] = s_cnt > cap ? (int32_t)cap + 1 : s_cnt;
+}
+
+// K2b: one pass over a tile of masks evaluates the predicates of up to
+// kGatherQPB other leaders (boolean filters, or subset filters with no
+// required bit) and appends the passing ids to their lists.
 __global__ void __launch_bounds__(256)
-gather_list_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, const int32_t *leaders,
+gather_list_kernel(DevIndex ix, const jag_filter *filters, const uint8_t *aux, const int32_t *leaders, int64_t nq,
                    const unsigned long long *nlead, int64_t cap, int32_t *lists, int32_t *counts) {
   __shared__ uint64_t sm[kGatherTile];
   const int64_t t0 = (int64_t)blockIdx.x * kGatherTile;
   const int64_t t1 = min64(ix.n, t0 + kGatherTile);
   const int64_t q0 = (int64_t)blockIdx.y * kGatherQPB;
-  const int64_t nl = (int64_t)*nlead;
+  const int64_t nl = (int64_t)*nlead;   // the leaders at leaders[0 .. nl) (the back of the array)
   if (q0 >= nl) return;
   for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) sm[i - t0] = ix.a_mask[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int qq = warp; qq < kGatherQPB; qq += nw) {
     if (q0 + qq >= nl) break;
-    const int64_t qi = leaders[q0 + qq];
+    const int64_t qi = leaders[nq - 1 - (q0 + qq)];
     const jag_filter f = filters[qi];
     const uint8_t *tt = f.kind == JAG_F_BOOL ? aux + f.aux_off : nullptr;
     for (int64_t b = t0; b < t1; b += 32) {
@@ -768,11 +830,15 @@ cudaError_t run_search(const SearchLaunch &L) {
     if ((e = cudaMemsetAsync(L.lgroup.hlead, 0x7F, L.lgroup.slots * 4, L.stream)) != cudaSuccess) return e;
     list_group_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.filters, L.aux, L.nq, L.lgroup.hkey, L.lgroup.hlead,
                                                 (uint32_t)(L.lgroup.slots - 1), L.lgroup.lslot);
-    list_leader_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.nq, L.lgroup.hlead, L.lgroup.lslot, L.lgroup.leaders,
-                                                 L.work + 8);
+    list_leader_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.filters, L.nq, L.lgroup.hlead, L.lgroup.lslot,
+                                                 L.lgroup.leaders, L.work + 8);
+    gather_postings_kernel<<<(unsigned)L.nq, kPostWarps * 32, 0, L.stream>>>(
+        L.ix, L.filters, L.lgroup.leaders, L.work + 8, L.cap, L.lists, L.list_counts);
+    // the other leaders sit at the back of the array, in reverse order: the
+    // mask pass reads them as leaders[nq - 1 - i]
     dim3 grid((unsigned)((L.ix.n + kGatherTile - 1) / kGatherTile), (unsigned)((L.nq + kGatherQPB - 1) / kGatherQPB));
-    gather_list_kernel<<<grid, 256, 0, L.stream>>>(L.ix, L.filters, L.aux, L.lgroup.leaders, L.work + 8, L.cap,
-                                                   L.lists, L.list_counts);
+    gather_list_kernel<<<grid, 256, 0, L.stream>>>(L.ix, L.filters, L.aux, L.lgroup.leaders, L.nq, L.work + 9,
+                                                   L.cap, L.lists, L.list_counts);
     finalize_routes_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.plans, L.list_counts, L.nq,
                                                                                  L.cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
