@@ -1,19 +1,28 @@
 """Benchmark: QPS at recall@10 >= 0.95 per selectivity band, JAG filtered
 search on one GB300 (N GPUs: one replica and one query batch per rank).
 
-Workload (synthetic stand-in for the paper's label-filter datasets): N=1,000,000
-base vectors, d=128, fp32, from a 100-component Gaussian mixture (centres
-N(0,4I), unit covariance); one label per point, Zipf(1.1) over 1,000 labels;
-10,000 queries from the same mixture with labels from the same law; k=10,
-graph degree R=32, build beam 64, thresholds {100%, 0%}, alpha 1.2; labels
-with fewer than 10,000 points (selectivity < 1%) go to the exact scan.
+Headline workload (synthetic stand-in for the paper's label-filter datasets):
+N=1,000,000 base vectors, d=128, fp32, from a 100-component Gaussian mixture
+(centres N(0,4I), unit covariance); one label per point, Zipf(1.1) over 1,000
+labels; 10,000 queries from the same mixture with labels from the same law;
+k=10, graph degree R=32, build beam 64, thresholds {100%, 0%}, alpha 1.2;
+labels with fewer than 16,384 points go to the exact scan (on the tensor
+cores).
 
 A step = one jag_search call over the whole 10,000-query batch: filter
 preparation and routing, graph search (Algorithm 2) for graph-routed
 queries, exact scan for the most selective ones.  The beam is the smallest of
-16..256 for which recall@10 (against the GPU brute-force scan) is >= 0.95 in
-every selectivity band.  Inputs (640 MB of vectors + graph) exceed the L2
-cache, and L2 is also flushed between timed steps.
+16..256 for which recall@10 (against the exact scan of every query, itself
+checked against the oracle's brute force on a sample) is >= 0.95 in every
+selectivity band.  Inputs (640 MB of vectors + graph) exceed the L2 cache,
+and L2 is also flushed between timed steps.
+
+The same JSON line also carries the other forms: BF16 / FP8 rows and the
+learned stop policy on the label workload; the learned beam / stop network
+on the mixed range / boolean workload (two graphs, 100,000 training
+queries); the precision form on subset filters (d = 100, fp32 / BF16 / FP8
+rows); the 10M-point BF16 serving form with the serve loop's p50 / p99; the
+serve loop on the label index; and the oracle on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
