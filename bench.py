@@ -6,7 +6,7 @@ N=1,000,000 base vectors, d=128, fp32, from a 100-component Gaussian mixture
 (centres N(0,4I), unit covariance); one label per point, Zipf(1.1) over 1,000
 labels; 10,000 queries from the same mixture with labels from the same law;
 k=10, graph degree R=32, build beam 64, thresholds {100%, 0%}, alpha 1.2;
-labels with fewer than 16,384 points go to the exact scan (on the tensor
+labels with fewer than 8,192 points go to the exact scan (on the tensor
 cores).
 
 A step = one jag_search call over the whole 10,000-query batch: filter
@@ -50,8 +50,9 @@ R = 32
 LB = 64
 THRESHOLDS = (100, 0)
 ALPHA = 1.2
-S0 = 16384         # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
-SCAN_CAP = 16384
+S0 = 8192          # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
+SCAN_CAP = 8192
+SERVE_S0 = 2048    # the serve loop scans a passing set with one warp (fp32 fma), so it takes smaller ones
 
 
 def workload_desc(n, d, nq):
@@ -956,7 +957,7 @@ def serve_saturation(jag, idx, w, beam, batch_qps, n_req=2000, offered=(0.6, 0.8
         sizes = rng.integers(1, 257, n_req).astype(np.int32)
         first = np.array([rng.integers(0, len(w.q) - s + 1) for s in sizes], np.int64)
         arrival = np.cumsum(rng.exponential(float(sizes.mean()) / (frac * batch_qps), n_req))
-        srv = jag.Server(idx, K, beam, s0=S0, scan_cap=SCAN_CAP, max_queries=1 << 17)
+        srv = jag.Server(idx, K, beam, s0=SERVE_S0, scan_cap=SCAN_CAP, max_queries=1 << 17)
         t1 = time.perf_counter()
         srv.replay(arrival, sizes, first, w.q, w.filters, w.aux, timeout_s=300.0)
         wall = time.perf_counter() - t1
@@ -971,14 +972,14 @@ def measure_serving(jag, idx, w, beam, band, gt_ids, gt_d, batch_qps, n_req=2000
     fraction of the loop's own saturated throughput; p50 / p99 latency from
     arrival to completion, achieved QPS, and recall per band."""
     sat_qps = serve_saturation(jag, idx, w, beam, batch_qps)
-    out = {"saturated_qps": round(sat_qps, 1)}
+    out = {"saturated_qps": round(sat_qps, 1), "s0": SERVE_S0}
     rng = np.random.default_rng(0)
     for load in loads:
         sizes = rng.integers(1, 257, n_req).astype(np.int32)
         first = np.array([rng.integers(0, len(w.q) - s + 1) for s in sizes], np.int64)
         rate = load * sat_qps / float(sizes.mean())            # requests per second
         arrival = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        srv = jag.Server(idx, K, beam, s0=S0, scan_cap=SCAN_CAP, max_queries=1 << 17)
+        srv = jag.Server(idx, K, beam, s0=SERVE_S0, scan_cap=SCAN_CAP, max_queries=1 << 17)
         t1 = time.perf_counter()
         ids, dist, lat, devs = srv.replay(arrival, sizes, first, w.q, w.filters, w.aux, timeout_s=300.0)
         wall = time.perf_counter() - t1
