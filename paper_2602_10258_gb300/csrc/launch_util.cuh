@@ -16,6 +16,9 @@ inline int blocks_per_sm(Kern kern, size_t smem, int warps = kSearchWarps) {
   static std::mutex mu;
   std::lock_guard<std::mutex> g(mu);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // all of the unified L1 / shared storage may go to shared memory: the
+  // occupancy query (and the launch) then count with the largest carve-out
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, warps * 32, smem) != cudaSuccess) b = 0;
   return b > 0 ? b : 0;
