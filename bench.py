@@ -6,7 +6,7 @@ N=1,000,000 base vectors, d=128, fp32, from a 100-component Gaussian mixture
 (centres N(0,4I), unit covariance); one label per point, Zipf(1.1) over 1,000
 labels; 10,000 queries from the same mixture with labels from the same law;
 k=10, graph degree R=32, build beam 64, thresholds {100%, 0%}, alpha 1.2;
-labels with fewer than 8,192 points go to the exact scan (on the tensor
+labels with fewer than 16,384 points go to the exact scan (on the tensor
 cores).
 
 A step = one jag_search call over the whole 10,000-query batch: filter
@@ -50,9 +50,9 @@ R = 32
 LB = 64
 THRESHOLDS = (100, 0)
 ALPHA = 1.2
-S0 = 8192          # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
-SCAN_CAP = 8192
-SERVE_S0 = 2048    # the serve loop scans a passing set with one warp (fp32 fma), so it takes smaller ones
+S0 = 16384         # a label slice is scanned when it holds fewer rows than this and at most SCAN_CAP
+SCAN_CAP = 16384
+SERVE_S0 = 8192    # the serve loop scans a passing set with one warp (fp32 fma), so it takes smaller ones
 
 
 def workload_desc(n, d, nq):

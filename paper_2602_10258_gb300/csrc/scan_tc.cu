@@ -635,8 +635,18 @@ cudaError_t launch_scan_tc(const SearchLaunch &L) {
   tc_items_kernel<<<(unsigned)((tu.U + 255) / 256), 256, 0, L.stream>>>(tu, T.tcnt, L.plans, T.ioff, T.item_unit);
   tc_qnorm_kernel<<<wb, 256, 0, L.stream>>>(L.plans, L.queries, L.d, nq, T.qnorm);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int bps = blocks_per_sm(tc_contract_kernel, kTcSmem, kTcThreads / 32);
+  int bps = blocks_per_sm(tc_contract_kernel, kTcSmem, kTcThreads / 32);
   if (bps == 0) return cudaErrorInvalidConfiguration;
+  {
+    // CTAs that fit an SM by shared memory (the occupancy query can report
+    // fewer for this kernel); the CTAs only claim items from a counter and
+    // never wait on one another, so more of them than fit at once is safe
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int by_smem = per_sm / (int)(kTcSmem + 4096);
+    bps = std::max(bps, std::min(by_smem, 2));
+  }
   tc_contract_kernel<<<(unsigned)(bps * num_sms()), kTcThreads, kTcSmem, L.stream>>>(
       L.ix, L.queries, L.d, L.filters, L.plans, L.lists, L.cap, tu, T.tcnt, T.toff, T.tq, T.ioff, T.item_unit,
       T.qnorm, L.work + 4, T.approx, L.status);

@@ -1,6 +1,6 @@
 """Parity at full size: the label workload the benchmark times (N=1,000,000,
 d=128, 10,000 queries, k=10, R=32, thresholds {100%, 0%}) in the benchmark's
-launch configurations: one jag_search over the whole batch with s0 = 8,192
+launch configurations: one jag_search over the whole batch with s0 = 16,384
 at the beams the benchmark measures -- FP32 at 192, BF16 at 192, FP8 at 224,
 and BF16 with a beam / stop policy at base beam 192.
 
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 jag = pytest.importorskip("paper_2602_10258_gb300.jag")
 
-N, NQ, K, BEAM, S0, CAP = 1_000_000, 10_000, 10, 192, 8192, 8192
+N, NQ, K, BEAM, S0, CAP = 1_000_000, 10_000, 10, 192, 16384, 16384
 
 
 @pytest.fixture(scope="module")

@@ -1,10 +1,10 @@
 """Parity at full size on the precision form's workload: N=1,000,000, d=100
 from a 200-component Gaussian mixture, a 64-bit label mask per point (bit j
 set with probability 0.5/(j+1)), 10,000 subset queries requiring 1-3 labels
-(selectivity 1e-4..0.5), k=10, R=32, the graph built on the masks (Hamming
-dist_A), rows stored as BF16 and as FP8-E4M3 with an fp32 re-rank of the
+(selectivity 1e-4..0.5), k=10, the benchmark's graph (Weight-JAG, R=64,
+weights {0, 1, 5}, Hamming dist_A), rows stored as BF16 and as FP8-E4M3 with an fp32 re-rank of the
 leading min(4k, beam) candidates, in the launch configuration the benchmark
-times (one jag_search over the batch, s0 = scan_cap = 8,192).
+times (one jag_search over the batch, s0 = scan_cap = 16,384).
 
 The graph comes from the GPU build (equal to the oracle build bit for bit at
 smaller sizes); on it, sampled queries are answered by the oracle one by one
@@ -21,13 +21,13 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 jag = pytest.importorskip("paper_2602_10258_gb300.jag")
 
-N, NQ, K, S0, CAP = 1_000_000, 10_000, 10, 8192, 8192
+N, NQ, K, S0, CAP = 1_000_000, 10_000, 10, 16384, 16384
 
 
 @pytest.fixture(scope="module")
 def full():
     w = D.make_subset(n=N, d=100, nq=NQ, seed=0)
-    gi = jag.Index.from_workload(w, R=32, l_b=64, alpha=1.2, thresholds=(100, 0))
+    gi = jag.Index.from_workload(w, R=64, l_b=64, alpha=1.2, weights=(0, 1, 5))
     info = gi.info()
     graph = gi.graph()
     gi.close()
@@ -38,14 +38,14 @@ def full():
                                                                                  "bf16-256", "fp8-256"])
 def test_subset_full_size_matches_oracle(full, fmt, beam):
     w, graph, entry = full
-    gi = jag.Index.from_workload(w, R=32, graph=graph, entry=entry, storage=fmt)
+    gi = jag.Index.from_workload(w, R=64, graph=graph, entry=entry, storage=fmt)
     q = torch.from_numpy(w.q).cuda()
     ids, dist, cnt = gi.search(q, w.filters, w.aux, K, beam, counters=True, s0=S0, scan_cap=CAP)
     torch.cuda.synchronize()
     ids, dist, cnt = ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
     gi.close()
     assert (cnt[:, 3] == 1).any() and (cnt[:, 3] == 0).any()        # both routes taken
-    ox = O.Index.from_workload(w, R=32, graph=graph, entry=entry, storage=fmt)
+    ox = O.Index.from_workload(w, R=64, graph=graph, entry=entry, storage=fmt)
     sample = np.random.default_rng(31 + fmt).choice(NQ, 32, replace=False)
     rid, rd, rc = O.query(ox, w.q[sample], w.filters[sample], w.aux, K, beam, s0=S0, scan_cap=CAP)
     assert (cnt[sample, 3] == rc[:, 3]).all()
