@@ -477,6 +477,7 @@ __device__ __forceinline__ void group_rows(const DevIndex &ix, const jag_filter 
 }
 
 // (3) selection per scan-routed query (one warp each), see the file comment.
+constexpr int kSelUnroll = 8;   // approximations read per lane per round
 template <int CAP, int P, int CPL>
 __global__ void __launch_bounds__(kSearchWarps * 32)
 tc_select_kernel(DevIndex ix, const float *queries, int d, const jag_filter *filters, const QueryPlan *plans,
@@ -508,13 +509,22 @@ tc_select_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
   float thr = INFINITY;
   if (m > 4 * (int64_t)k && k <= 128) {
     float r0 = INFINITY, r1 = INFINITY, r2 = INFINITY, r3 = INFINITY;
-    for (int64_t j = lane; j < m; j += 32) {
-      float v = a[j];
-      if (v < r3) {
-        r3 = v;
-        if (r3 < r2) { const float t = r2; r2 = r3; r3 = t; }
-        if (r2 < r1) { const float t = r1; r1 = r2; r2 = t; }
-        if (r1 < r0) { const float t = r0; r0 = r1; r1 = t; }
+    for (int64_t b = 0; b < m; b += 32 * kSelUnroll) {
+      float vv[kSelUnroll];   // kSelUnroll independent loads in flight per lane
+#pragma unroll
+      for (int r = 0; r < kSelUnroll; ++r) {
+        const int64_t j = b + r * 32 + lane;
+        vv[r] = j < m ? a[j] : INFINITY;
+      }
+#pragma unroll
+      for (int r = 0; r < kSelUnroll; ++r) {
+        const float v = vv[r];
+        if (v < r3) {
+          r3 = v;
+          if (r3 < r2) { const float t = r2; r2 = r3; r3 = t; }
+          if (r2 < r1) { const float t = r1; r1 = r2; r2 = t; }
+          if (r1 < r0) { const float t = r0; r0 = r1; r1 = t; }
+        }
       }
     }
     float tau = INFINITY;
@@ -537,34 +547,48 @@ tc_select_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
     bool broken = false;
     cnt = 0;
     ncand = 0;
-    for (int64_t b = 0; b < m; b += 32) {
-      const int64_t j = b + lane;
-      const float v = j < m ? a[j] : INFINITY;
-      const bool cand = j < m && !(v > thr);
-      const uint32_t cm = __ballot_sync(kFull, cand);
-      if (!cm) continue;
-      const int nc = __popc(cm);
-      ncand += nc;
-      if (cand) {
-        const int pos = __popc(cm & lanemask_lt());
-        S.cid[pos] = (uint32_t)ids[j];
-        S.ck1[pos] = f2u(v);   // its approximation, for the bound check
+    for (int64_t b0 = 0; b0 < m; b0 += 32 * kSelUnroll) {
+      float vv[kSelUnroll];
+      uint32_t any = 0;
+#pragma unroll
+      for (int r = 0; r < kSelUnroll; ++r) {
+        const int64_t j = b0 + r * 32 + lane;
+        vv[r] = j < m ? a[j] : INFINITY;
+        any |= (j < m && !(vv[r] > thr)) ? (1u << r) : 0u;
       }
-      __syncwarp();
-      const bool full = cnt == k;
-      const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
-      const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
-      const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
-      uint64_t ck = kNoKey;
-      uint32_t cv = kEmptySlot;
-      if (lane < nc) {
-        if (thr != INFINITY && !(fabsf(__fsub_rn(u2f(S.ck1[lane]), dist)) <= eps)) broken = true;
-        ck = make_key(0u, dist);
-        cv = S.cid[lane];
-        if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+      if (!__any_sync(kFull, any != 0)) continue;
+      for (int r = 0; r < kSelUnroll; ++r) {
+        const int64_t b = b0 + r * 32;
+        if (b >= m) break;
+        const bool cand = (any >> r) & 1u;
+        const uint32_t cm = __ballot_sync(kFull, cand);
+        if (!cm) continue;
+        float v = vv[0];   // vv[r] by selection, so that vv stays in registers
+#pragma unroll
+        for (int i = 1; i < kSelUnroll; ++i) v = r == i ? vv[i] : v;
+        const int nc = __popc(cm);
+        ncand += nc;
+        if (cand) {
+          const int pos = __popc(cm & lanemask_lt());
+          S.cid[pos] = (uint32_t)ids[b + lane];
+          S.ck1[pos] = f2u(v);   // its approximation, for the bound check
+        }
+        __syncwarp();
+        const bool full = cnt == k;
+        const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
+        const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
+        const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+        uint64_t ck = kNoKey;
+        uint32_t cv = kEmptySlot;
+        if (lane < nc) {
+          if (thr != INFINITY && !(fabsf(__fsub_rn(u2f(S.ck1[lane]), dist)) <= eps)) broken = true;
+          ck = make_key(0u, dist);
+          cv = S.cid[lane];
+          if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
+        }
+        int r0;
+        cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
       }
-      int r0;
-      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
     }
     if (!__any_sync(kFull, broken)) break;
     if (lane == 0) atomicOr(status, kErrTcBound);

@@ -366,3 +366,33 @@ def test_large_beam_rejected_where_unsupported(range_small):
         gi.search(q, w.filters[:4], w.aux, 10, 300, s0=0, policy=pol)
     with pytest.raises(jag.JagError):
         jag.Server(gi, 10, 300)
+
+
+@pytest.mark.parametrize("d", [3, 7, 33, 130, 256, 700])
+def test_scan_route_row_layouts(d):
+    """The exact scan at dimensions that are not a multiple of the tensor
+    core's K step (8 elements), that span several K passes of 128, or both:
+    every query goes to the scan (about 900 passing rows each, so the
+    threshold selection runs) and must equal the oracle's brute force."""
+    n = 3000
+    w = D.make_range_i32(n=n, d=d, nq=40, seed=40 + d, width=300)
+    ox = O.Index.from_workload(w, R=16)
+    gi = jag.Index.from_workload(w, R=16, graph=np.full((n, 16), -1, np.int32), entry=0)
+    ids, dist, cnt = gpu_search(gi, w.q, w.filters, w.aux, 10, 32, s0=100_000, scan_cap=100_000)
+    assert (cnt[:, 3] == 1).all()
+    assert (cnt[:, 1] < cnt[:, 2]).mean() > 0.9          # the threshold narrowed the candidates
+    bi, bd, _, _ = O.brute_force(ox, w.q, w.filters, w.aux, 10)
+    assert (ids == bi).all()
+    assert np.array_equal(dist.view(np.uint32), bd.view(np.uint32))
+    gi.close()
+
+
+def test_scan_route_large_k(range_small):
+    """k above 128: every passing row is a candidate of the exact scan."""
+    w, ix, _, gi = range_small
+    q, f = w.q[:30], w.filters[:30]
+    ids, dist, cnt = gpu_search(gi, q, f, w.aux, 200, 256, s0=100_000, scan_cap=100_000)
+    assert (cnt[:, 3] == 1).all() and (cnt[:, 1] == cnt[:, 2]).all()
+    bi, bd, _, _ = O.brute_force(ix, q, f, w.aux, 200)
+    assert (ids == bi).all()
+    assert np.array_equal(dist.view(np.uint32), bd.view(np.uint32))
