@@ -461,6 +461,10 @@ def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stre
             break
     if chosen is None:
         chosen = BEAMS[-1]
+    cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev)
+    jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, cnt, stream, s0=S0, scan_cap=SCAN_CAP)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
     for _ in range(3):
         jag.jag_search(idx.h, q, ft, at, K, chosen, ids, dd, None, stream, s0=S0, scan_cap=SCAN_CAP)
     ts, ks = [], []
@@ -477,8 +481,14 @@ def measure_form(jag, idx, q, ft, at, nq, band, gt_ids, gt_d, steps, flush, stre
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b, _, _ in ts]))
     kms = float(np.mean([ka.elapsed_time(kb) for _, _, ka, kb in ts]))
+    info = idx.info()
+    row_bytes = (info["d"] * 2 + 15) // 16 * 16 if info["storage"] == 1 else (info["d"] + 15) // 16 * 16 + 4
+    gbytes = mixed_graph_bytes(c, row_bytes, 4, R)
     return {"beam": chosen, "qps": round(nq / (ms / 1000.0), 1), "ms_per_step": round(ms, 4),
-            "graph_kernel_ms": round(kms, 3), "recall": per, "steps": steps}
+            "graph_kernel_ms": round(kms, 3), "recall": per, "steps": steps,
+            "graph_kernel_gather_bytes": gbytes,
+            "graph_kernel_frac_of_hbm": round(gbytes / (kms / 1e3) / 1e9 / measured_peaks()[0], 4),
+            "gather_bytes_source": "the kernel's counters (hops, first-seen neighbours, distances)"}
 
 
 def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_ids, gt_d, flush, stream,
@@ -503,7 +513,7 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
     dd = torch.empty((nq, K), dtype=torch.float32, device=dev)
     cnt = torch.empty((nq, 4), dtype=torch.int32, device=dev)
     t0 = time.time()
-    cands = []
+    cands, best_cnt = [], {}
     for base in (192, 224, 256):
         forced = torch.tensor([[base, 0]], dtype=torch.int32, device=dev).repeat(n_train, 1)
         feats = torch.zeros((n_train, 12), dtype=torch.float32, device=dev)
@@ -526,6 +536,7 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
                    if ((band == j) & ~np.isnan(rec)).any()}
             c = cnt.cpu().numpy()
             g = c[:, 3] == 0
+            best_cnt[(base, scale)] = c
             cands.append((base, scale, lp, per, float(c[g, 0].mean()), float(trace[-1])))
     ok = [cd for cd in cands if all(v >= 0.95 for v in cd[3].values())]
     train_s = time.time() - t0
@@ -554,8 +565,12 @@ def measure_learned(jag, w, graph_host, entry, local, q, ft, at, nq, band, gt_id
         return {"qps": None, "note": "no (base, scale) reached recall 0.95 in every band",
                 "train_seconds": round(train_s, 1)}
     ms, base, scale, per, hops, loss = best
+    c = best_cnt[(base, scale)]
+    gbytes = mixed_graph_bytes(c, (w.d * 2 + 15) // 16 * 16, 4, R)
     return {"beam": base, "stop_scale": scale, "h0": 32, "qps": round(nq / (ms / 1000.0), 1),
             "ms_per_step": round(ms, 4), "recall": per, "mean_hops_graph_route": round(hops, 1),
+            "gather_bytes_per_step": gbytes,
+            "gather_frac_of_hbm_over_step": round(gbytes / (ms / 1e3) / 1e9 / measured_peaks()[0], 4),
             "train": {"queries": n_train, "epochs": 60, "final_loss": round(loss, 4), "seconds": round(train_s, 1)},
             "steps": steps}
 
