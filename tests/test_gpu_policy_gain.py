@@ -72,3 +72,57 @@ def test_learned_stop_beats_a_uniform_stop_at_equal_hops():
     assert r_learned > r_uniform
     assert hops_l < 0.9 * plain_cnt[:, 0].mean()
     assert r_learned > r_plain - 0.05
+
+
+def test_learned_beam_saves_hops_on_mixed_filters():
+    """The beam head on the mixed workload (float ranges on one graph,
+    boolean filters on a graph built on the mask): trained on traces of
+    20,000 training queries labelled with the smallest ladder beam that
+    reaches recall 0.95 (raised one ladder step as a margin), the network's
+    beams make the graph searches shorter than the plain search at the same
+    base beam, and recall stays within 0.02 of the plain search's."""
+    n, base = 200_000, 192
+    ladder = (32, 48, 64, 96, 128, 160, 192, 224, 256)
+    nl = len(ladder)
+    w = D.make_mixed(n=n, d=64, nq=3000, seed=5, n_centres=40)
+    wt = D.make_mixed(n=n, d=64, nq=20000, seed=5, n_centres=40, query_seed=105)
+    dev = torch.device("cuda")
+    graphs = {jag.JAG_F_RANGE_F32: (100, 10, 0), jag.JAG_F_BOOL: (100, 1, 0)}
+    hops_plain, hops_learned, rec_plain, rec_learned = [], [], [], []
+    traces, idx = [], {}
+    for kind, thr in graphs.items():
+        ix = jag.Index(w.x, attr_f32=w.attr_f32, attr_mask=w.attr_mask, dist_a=kind, R=64, l_b=64, thresholds=thr)
+        idx[kind] = ix
+        rows_t = np.nonzero(wt.filters["kind"] == kind)[0]
+        qt = torch.from_numpy(np.ascontiguousarray(wt.q[rows_t])).to(dev)
+        ft = jag.filters_to_device(wt.filters[rows_t], dev)
+        at = jag.aux_to_device(wt.aux, dev)
+        gt_t, _ = PL.exact_answers(ix, qt, ft, at, K)
+        traces.append(PL.collect_traces(ix, qt, ft, at, K, base, gt_t, ladder=ladder, h0=16))
+    tr = PL.concat_traces(traces)
+    y, t = tr.labels(target=0.95, stop_margin=1.25, stop_extra=8)
+    y = np.minimum(y + 1, nl - 1).astype(np.int32)
+    keep = ~np.isnan(tr.recall).any(1)
+    order = np.random.default_rng(0).permutation(np.nonzero(keep)[0])
+    params = torch.from_numpy(D.mlp_init_params(nl, 1)).to(dev)
+    jag.Trainer(nl, params).run(torch.from_numpy(np.ascontiguousarray(tr.X[order])).to(dev),
+                                torch.from_numpy(y[order]).to(dev), torch.from_numpy(t[order]).to(dev),
+                                epochs=40, batch=512, lr=2e-3, lam=0.25)
+    pol = jag.Policy.learned(params, ladder=ladder, h0=16, tau=0.0, stop_scale=0.0)
+    for kind, ix in idx.items():
+        rows = np.nonzero(w.filters["kind"] == kind)[0]
+        q = torch.from_numpy(np.ascontiguousarray(w.q[rows])).to(dev)
+        f = jag.filters_to_device(w.filters[rows], dev)
+        a = jag.aux_to_device(w.aux, dev)
+        gt, _ = PL.exact_answers(ix, q, f, a, K)
+        for p, hops, rec in ((None, hops_plain, rec_plain), (pol, hops_learned, rec_learned)):
+            ids, _, cnt = ix.search(q, f, a, K, base, counters=True, s0=0, policy=p)
+            torch.cuda.synchronize()
+            hops.append(cnt.cpu().numpy()[:, 0])
+            rec.append(PL.recall_rows(ids.cpu().numpy(), gt, K))
+        ix.close()
+    hp, hl = np.concatenate(hops_plain).mean(), np.concatenate(hops_learned).mean()
+    rp, rl = np.nanmean(np.concatenate(rec_plain)), np.nanmean(np.concatenate(rec_learned))
+    print("plain: %.1f hops, recall %.4f | learned beams: %.1f hops, recall %.4f" % (hp, rp, hl, rl))
+    assert hl < 0.9 * hp
+    assert rl > rp - 0.02
