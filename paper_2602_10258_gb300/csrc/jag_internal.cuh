@@ -187,6 +187,13 @@ __device__ __forceinline__ uint64_t ld_dword(const void *p) {
   return v;
 }
 
+// Ask L2 for the 128-byte lines of [p, p + bytes) (no register is written;
+// a later load of the bytes finds them in L2 or already on their way).
+__device__ __forceinline__ void prefetch_l2(const void *p, int bytes) {
+  const uint64_t a1 = ((uint64_t)p + (uint64_t)bytes - 1) & ~127ull;
+  for (uint64_t a = (uint64_t)p & ~127ull; a <= a1; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // The same word for the target of edge e (= p * R + r) from the edge table;
 // issued where it is written, next to the load of the neighbour id.
 __device__ __forceinline__ uint64_t edge_attr(const DevIndex &ix, int64_t e, int32_t kind) {
@@ -226,7 +233,7 @@ __device__ __forceinline__ uint32_t capped_distance(int32_t dist_a, uint32_t da,
 }
 
 __device__ __forceinline__ bool key_less(uint64_t ak, uint32_t aid, uint64_t bk, uint32_t bid) {
-  return ak < bk || (ak == bk && aid < bid);
+  return (ak < bk) | ((ak == bk) & (aid < bid));   // no short circuit: no branch
 }
 
 __device__ __forceinline__ uint64_t make_key(uint32_t first, float dist) {
@@ -311,18 +318,38 @@ __device__ __forceinline__ float group_reduce(float acc) {
   return acc;
 }
 
-// The same butterfly for U independent accumulators, interleaved step by
-// step so that their shuffle chains overlap.
+// The same butterfly for U accumulators (U a power of two, U <= P), with the
+// rows spread over the lanes as they are reduced: at each of the first
+// log2(U) levels a lane keeps half of its rows (the lower half if bit o of
+// its lane index is clear) and trades the other half with lane l xor o, so
+// one shuffle moves two partial rows.  Every row still receives the sums
+// acc_l + acc_(l xor o) of the plain butterfly (fp32 addition is
+// commutative), in the same tree, with U - 1 + log2(P/U) shuffles instead of
+// U log2(P).  On return lane l of a group holds the total of row
+// (l mod P) / (P/U); spread_source gives the lane holding row s of group g.
 template <int P, int U>
-__device__ __forceinline__ void group_reduce_n(float (&acc)[U]) {
+__device__ __forceinline__ float group_reduce_spread(float (&acc)[U]) {
+  static_assert(U >= 1 && (U & (U - 1)) == 0 && U <= P, "rows per lane");
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = P / 2; o >= 1; o >>= 1) {
-    float t[U];
+  for (int h = U / 2, o = P / 2; h >= 1; h >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) t[u] = __shfl_xor_sync(kFull, acc[u], o);
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = __fadd_rn(acc[u], t[u]);
+    for (int i = 0; i < h; ++i) {
+      const float send = upper ? acc[i] : acc[i + h];
+      const float keep = upper ? acc[i + h] : acc[i];
+      acc[i] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, o));
+    }
   }
+  float v = acc[0];
+#pragma unroll
+  for (int o = P / (2 * U); o >= 1; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+template <int P, int U>
+__device__ __forceinline__ int spread_source(int s, int g) {
+  return g * P + s * (P / U);
 }
 
 // Status word bits written by kernels (read back by the host where needed).

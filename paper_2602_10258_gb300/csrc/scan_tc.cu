@@ -587,7 +587,7 @@ tc_select_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
           if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
         }
         int r0;
-        cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+        cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
       }
     }
     if (!__any_sync(kFull, broken)) break;

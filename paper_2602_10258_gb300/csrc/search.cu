@@ -268,13 +268,11 @@ __device__ __forceinline__ float staged_distances(const QChunks<CPL, JAG_VEC_F32
         }
       }
     }
-    group_reduce_n<P, U>(acc);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int c0 = base + u * VPW;
-      const float v = __shfl_sync(kFull, acc[u], ((lane - c0) * P) & 31);
-      if (lane >= c0 && lane < c0 + VPW) mine = v;
-    }
+    const float tot = group_reduce_spread<P, U>(acc);
+    const int rel = lane - base;
+    const bool mine_here = rel >= 0 && rel < VPW * U;
+    const float v = __shfl_sync(kFull, tot, mine_here ? spread_source<P, U>(rel / VPW, rel % VPW) : 0);
+    if (mine_here) mine = v;
   }
   return mine;
 }
@@ -368,7 +366,7 @@ scan_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fil
         if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
       }
       int r0;
-      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
       __syncwarp();   // rows[cur] and cids[cur] are reused by round r + 2
     }
     uint64_t *pk = part_key + (qi * ntiles + t) * k;
@@ -427,7 +425,7 @@ merge_scan_kernel(const DevIndex ix, const jag_filter *filters, const QueryPlan 
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
       int r0;
-      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -482,7 +480,7 @@ brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fi
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
     int r0;
-    cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+    cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
   }
   for (int j = lane; j < k; j += 32) {
     pk[j] = j < cnt ? S.bkey[j] : kNoKey;
@@ -511,7 +509,7 @@ merge_parts_kernel(const QueryPlan *plans, int64_t nq, int k, int ntiles, const 
       }
       if (cnt == k && ck != kNoKey && !key_less(ck, cv, S.bkey[k - 1], S.bid[k - 1])) { ck = kNoKey; cv = kEmptySlot; }
       int r0;
-      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
     }
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
@@ -557,7 +555,7 @@ rerank_kernel(DevIndex ix, const float *queries, int d, const QueryPlan *plans, 
       if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
     }
     int r0;
-    cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+    cnt = merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
   }
   write_answers(S, cnt, qi, k, out_ids, out_dist);
 }

@@ -19,9 +19,10 @@
 //            skip steps that would add exact zeros);
 //   merge    each surviving neighbour's position in the merged list is its
 //            rank in L (a fixed-step binary search) plus the number of
-//            smaller new keys; entries of L move right in 32-wide chunks
-//            taken from the back; the best l_s are kept and a neighbour
-//            already in L (equal key and id) is dropped;
+//            smaller new keys; L is rebuilt from the back, 32 positions at a
+//            time, each lane fetching the entry that lands on its position;
+//            the best l_s are kept and a neighbour already in L (equal key
+//            and id) is dropped;
 // until every entry of L is expanded.
 //
 // The visited set may forget (a new id replaces the first of its two probe
@@ -34,6 +35,11 @@
 
 namespace jag {
 
+// Whether the graph search asks L2 for the rows of a hop's candidates past
+// its first batch of loads before it starts the batches.  Requesting the
+// out-list of the likely next vertex (the second unexpanded entry of L) was
+// measured slower for every format.
+__host__ __device__ constexpr bool prefetch_rows(int FMT) { return FMT != JAG_VEC_FP8; }
 constexpr int kSearchWarps = 4;   // warps (searches) per CTA of the search kernels (the graph kernel: graph_warps)
 
 // Shared-memory slice of one warp.
@@ -43,7 +49,7 @@ struct WarpSmem {
   uint32_t *hash;   // [1 << hbits] visited set
   uint32_t *cid;    // [32] candidate ids of the current hop
   uint32_t *ck1;    // [32] their first keys
-  uint32_t *rank;   // [32] merge ranks
+  uint32_t *rank;   // [32] scratch (anchors the policy context)
 };
 
 // Slots of a warp's list for beam ls: ls rounded up to a multiple of 32.
@@ -84,28 +90,31 @@ __device__ __forceinline__ int first_unexpanded(const uint32_t *bid, int cnt, in
 __device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t id) {
   const uint32_t mask = (1u << hbits) - 1;
   const uint32_t h = (id * 0x9E3779B1u) >> (32 - hbits);
-  uint32_t old = atomicCAS(&tab[h], kEmptySlot, id);
-  if (old == kEmptySlot) return true;
-  if (old == id) return false;
-  old = atomicCAS(&tab[(h + 1) & mask], kEmptySlot, id);
-  if (old == kEmptySlot) return true;
-  if (old == id) return false;
-  atomicExch(&tab[h], id);
-  return true;
+  const uint32_t old = atomicCAS(&tab[h], kEmptySlot, id);
+  bool fresh = old == kEmptySlot;
+  if ((old != kEmptySlot) & (old != id)) {   // the first slot holds another id
+    const uint32_t o2 = atomicCAS(&tab[(h + 1) & mask], kEmptySlot, id);
+    fresh = o2 != id;
+    if ((o2 != kEmptySlot) & (o2 != id)) atomicExch(&tab[h], id);
+  }
+  return fresh;
 }
 
-// Number of entries of the sorted list L[0..cnt) that precede (k, id): a
-// binary search with a fixed number of steps, so that every lane runs the
-// same instructions.
-template <int CAP>
+// Number of entries of the sorted list L[0..cnt) (cnt >= 1) that precede
+// (k, id): a binary search with a fixed number of steps and no branch, so
+// that every lane runs the same instructions.  TOP is the first step: CAP,
+// or CAP / 2 where the caller knows the key precedes L's last entry when L
+// holds CAP entries.  (A 4-way search, three probes a step, halves the chain
+// of dependent reads but was measured slower: it issues more instructions.)
+template <int TOP>
 __device__ __forceinline__ int list_rank(const uint64_t *bkey, const uint32_t *bid, int cnt, uint64_t k,
                                          uint32_t id) {
   int pos = 0;
 #pragma unroll
-  for (int step = CAP; step >= 1; step >>= 1) {
+  for (int step = TOP; step >= 1; step >>= 1) {
     const int probe = pos + step;
-    const int j = max(min(probe, cnt) - 1, 0);
-    const bool before = probe <= cnt && key_less(bkey[j], bid[j] & ~kExpanded, k, id);
+    const int j = min(probe, cnt) - 1;
+    const bool before = (probe <= cnt) & key_less(bkey[j], bid[j] & ~kExpanded, k, id);
     pos = before ? probe : pos;
   }
   return pos;
@@ -115,21 +124,29 @@ __device__ __forceinline__ int list_rank(const uint64_t *bkey, const uint32_t *b
 // into L[0..cnt): keep the best ls, drop candidates already in L.  Returns
 // the new count; r0 receives the smallest insertion position (cnt if none).
 //
-// BSEARCH: an entry's shift is found by a 5-step search of the new keys'
-// sorted ranks (srank, 32 words of shared memory) -- cheaper for the long
-// lists of the graph search; otherwise by one shuffle per new key -- smaller
-// code, better for the k-entry lists of the exact scans.
-template <int CAP, bool BSEARCH = true>
+// A new key's position in the merged list is its rank in L plus the number
+// of smaller new keys.  DEST (the long lists of the graph search): the list
+// is rebuilt by destination, 32 positions at a time from the back -- a
+// window's new-key positions are one OR-reduction of bits, so each lane
+// finds the old entry that lands on its position (its index minus the new
+// keys before it) and moves it; reads of a window stay at or below it and
+// writes at or above it, so no entry is overwritten before it is read.
+// Otherwise (the k-entry lists of the exact scans) an entry's shift is
+// counted with one shuffle per new key: smaller code.
+template <int CAP, bool DEST = true>
 __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, int cnt, int ls, uint64_t ck,
-                                                uint32_t cv, int &r0, uint32_t *srank) {
+                                                uint32_t cv, int &r0) {
   const int lane = threadIdx.x & 31;
   bool valid = ck != kNoKey;
   r0 = cnt;
   if (!__any_sync(kFull, valid)) return cnt;
-  const int rank = list_rank<CAP>(bkey, bid, cnt, ck, cv);
-  if (valid) {
-    if (rank >= ls) valid = false;
-    else if (rank < cnt && bkey[rank] == ck && (bid[rank] & ~kExpanded) == cv) valid = false;
+  // the graph search drops a key that follows a full list's last entry
+  // before the merge, so its ranks stay below CAP
+  const int rank = cnt == 0 ? 0 : list_rank<DEST ? CAP / 2 : CAP>(bkey, bid, cnt, ck, cv);
+  {
+    const int rr = min(rank, cnt - 1);   // a key equal to L's entry at its rank is a repeat
+    const bool rep = (rank < cnt) & (bkey[rr] == ck) & ((bid[rr] & ~kExpanded) == cv);
+    valid = valid & (rank < ls) & !rep;
   }
   const uint32_t vm = __ballot_sync(kFull, valid);
   r0 = cnt;
@@ -142,62 +159,42 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
     crank += key_less(ok, oi, ck, cv) ? 1 : 0;
   }
   r0 = (int)__reduce_min_sync(kFull, valid ? (unsigned)rank : 0xFFFFFFFFu);
-  if (BSEARCH) {
-    // the new keys' ranks in L, in the new keys' order (non-decreasing), padded
-    const int nv = __popc(vm);
-    if (valid) srank[crank] = (uint32_t)rank;
-    if (lane >= nv) srank[lane] = 0xFFFFFFFFu;
-    __syncwarp();
-  }
-  // entry j moves right by the number of new keys ranked at or before j (a
-  // 5-step search of srank); chunks from the back never overwrite an entry
-  // not yet read.  With the search, two chunks are read, searched and written
-  // per round: entries only move right, so a chunk's writes land at or past
-  // its own start, which the round has already read.
-  int t = (cnt - r0 + 31) / 32 - 1;
-  if (BSEARCH) {
-    for (; t >= 1; t -= 2) {
-      const int j1 = r0 + 32 * t + lane, j0 = j1 - 32;
-      uint64_t ek1 = 0, ek0 = 0;
-      uint32_t ei1 = 0, ei0 = 0;
-      if (j1 < cnt) { ek1 = bkey[j1]; ei1 = bid[j1]; }
-      ek0 = bkey[j0];
-      ei0 = bid[j0];
-      int sh1 = srank[31] <= (uint32_t)j1 ? 32 : 0, sh0 = srank[31] <= (uint32_t)j0 ? 32 : 0;
-#pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        if (sh1 < 32) sh1 += (srank[sh1 + step - 1] <= (uint32_t)j1) ? step : 0;
-        if (sh0 < 32) sh0 += (srank[sh0 + step - 1] <= (uint32_t)j0) ? step : 0;
+  const int n2 = min(cnt + __popc(vm), ls);
+  const int pos = rank + crank;   // distinct over the new keys
+  if (DEST) {
+    for (int f0 = r0 + ((n2 - 1 - r0) & ~31); f0 >= r0; f0 -= 32) {
+      const int f = f0 + lane;
+      const uint32_t inw = __reduce_or_sync(kFull, (valid && pos >= f0 && pos < f0 + 32) ? 1u << (pos - f0) : 0u);
+      const int below = __popc(__ballot_sync(kFull, valid && pos < f0));
+      const bool mv = f < n2 && !((inw >> lane) & 1u);
+      uint64_t ek = 0;
+      uint32_t ei = 0;
+      if (mv) {
+        const int j = f - below - __popc(inw & lanemask_lt());
+        ek = bkey[j];
+        ei = bid[j];
       }
       __syncwarp();
-      if (j1 < cnt && j1 + sh1 < ls) { bkey[j1 + sh1] = ek1; bid[j1 + sh1] = ei1; }
-      if (j0 + sh0 < ls) { bkey[j0 + sh0] = ek0; bid[j0 + sh0] = ei0; }
-      __syncwarp();
+      if (mv) { bkey[f] = ek; bid[f] = ei; }
     }
-  }
-  for (; t >= 0; --t) {
-    const int j = r0 + 32 * t + lane;
-    uint64_t ek = 0;
-    uint32_t ei = 0;
-    if (j < cnt) { ek = bkey[j]; ei = bid[j]; }
-    int sh = 0;
-    if (BSEARCH) {
-      sh = srank[31] <= (uint32_t)j ? 32 : 0;
-      if (sh == 0) {
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) sh += (srank[sh + step - 1] <= (uint32_t)j) ? step : 0;
-      }
-    } else {
+  } else {
+    // entry j moves right by the number of new keys ranked at or before j;
+    // chunks from the back never overwrite an entry not yet read
+    for (int t = (cnt - r0 + 31) / 32 - 1; t >= 0; --t) {
+      const int j = r0 + 32 * t + lane;
+      uint64_t ek = 0;
+      uint32_t ei = 0;
+      if (j < cnt) { ek = bkey[j]; ei = bid[j]; }
+      int sh = 0;
       for (uint32_t m = vm; m; m &= m - 1) sh += (__shfl_sync(kFull, rank, __ffs(m) - 1) <= j) ? 1 : 0;
+      __syncwarp();
+      if (j < cnt && j + sh < ls) { bkey[j + sh] = ek; bid[j + sh] = ei; }
+      __syncwarp();
     }
-    __syncwarp();
-    if (j < cnt && j + sh < ls) { bkey[j + sh] = ek; bid[j + sh] = ei; }
-    __syncwarp();
   }
-  if (valid && rank + crank < ls) { bkey[rank + crank] = ck; bid[rank + crank] = cv; }
+  if (valid && pos < ls) { bkey[pos] = ck; bid[pos] = cv; }
   __syncwarp();
-  const int n2 = cnt + __popc(vm);
-  return n2 < ls ? n2 : ls;
+  return n2;
 }
 
 // The lane-held chunks of a search point: lane lig of a P-lane group holds
@@ -206,6 +203,17 @@ template <int CPL, int FMT>
 struct QChunks {
   float4 v[CPL][RowFmt<FMT>::Q4];
 };
+
+// Start and length of stored row id in format FMT.
+template <int FMT>
+__device__ __forceinline__ const void *row_address(const DevIndex &ix, uint32_t id) {
+  return FMT == JAG_VEC_F32 ? static_cast<const void *>(ix.x + (int64_t)id * ix.xs)
+                            : static_cast<const void *>(ix.xq + (int64_t)id * ix.qbytes);
+}
+template <int FMT>
+__device__ __forceinline__ int row_bytes(const DevIndex &ix) {
+  return FMT == JAG_VEC_F32 ? ix.nchunks * 16 : ix.qbytes;
+}
 
 // Distances from the search point (lane-held chunks q) to the nc rows whose
 // ids are cid[0..nc), rows stored in format FMT; lane c < nc returns the
@@ -218,7 +226,7 @@ struct QChunks {
 // 16..P in registers before the shuffle levels P/2..1: the same additions in
 // the same order as the 32-lane canonical reduction (levels that would add
 // exact zeros are skipped).
-template <int P, int CPL, int ROWS = 4, int FMT = JAG_VEC_F32>
+template <int P, int CPL, int ROWS = 4, int FMT = JAG_VEC_F32, bool PREF = false>
 __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const QChunks<CPL, FMT> &q,
                                                      const uint32_t *cid, int nc) {
   constexpr int VPW = 32 / P;                        // rows per warp-wide load
@@ -228,53 +236,53 @@ __device__ __forceinline__ float candidate_distances(const DevIndex &ix, const Q
   const int lane = threadIdx.x & 31;
   const int grp = lane / P, lig = lane % P;
   const int nch = FMT == JAG_VEC_F32 ? ix.nchunks : ix.qchunks;
+  // rows past the first batch are requested from L2 at once (one lane per
+  // row), so that their loads below do not each wait a memory latency
+  if (PREF && nc > VPW * U && lane < nc - VPW * U)
+    prefetch_l2(row_address<FMT>(ix, cid[VPW * U + lane]), row_bytes<FMT>(ix));
   float mine = 0.f;
   for (int base = 0; base < nc; base += VPW * U) {
     uint4 xv[U][CPL];
     float sc[U];
+    // straight-line over the batch's U loads: a row past nc is not read (its
+    // chunks are zero) and its sum is never handed out
 #pragma unroll
     for (int s = 0; s < U; ++s) {
+      const int c = base + s * VPW + grp;
+      const bool ok = c < nc;
+      const uint32_t id = ok ? cid[c] : 0u;
+      const uint8_t *row = FMT == JAG_VEC_F32 ? reinterpret_cast<const uint8_t *>(ix.x + (int64_t)id * ix.xs)
+                                              : ix.xq + (int64_t)id * ix.qbytes;
       sc[s] = 1.f;
-      if (base + s * VPW < nc) {   // warp-uniform
-        const int c = base + s * VPW + grp;
-        const bool ok = c < nc;
-        const uint32_t id = ok ? cid[c] : 0u;
-        const uint8_t *row = FMT == JAG_VEC_F32 ? reinterpret_cast<const uint8_t *>(ix.x + (int64_t)id * ix.xs)
-                                                : ix.xq + (int64_t)id * ix.qbytes;
-        if (FMT == JAG_VEC_FP8) sc[s] = ok ? __ldg(ix.qscale + id) : 1.f;
+      if (FMT == JAG_VEC_FP8) sc[s] = ok ? __ldg(ix.qscale + id) : 1.f;
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-          const int ch = lig + j * P;
-          xv[s][j] = (ok && ch < nch) ? ld_chunk_u4(row + ch * 16) : make_uint4(0, 0, 0, 0);
-        }
+      for (int j = 0; j < CPL; ++j) {
+        const int ch = lig + j * P;
+        xv[s][j] = (ok && ch < nch) ? ld_chunk_u4(row + ch * 16) : make_uint4(0, 0, 0, 0);
       }
     }
     float acc[U];
 #pragma unroll
     for (int s = 0; s < U; ++s) {
-      acc[s] = 0.f;
-      if (base + s * VPW < nc) {   // warp-uniform
-        float a[NA];
+      float a[NA];
 #pragma unroll
-        for (int i = 0; i < NA; ++i) a[i] = 0.f;
+      for (int i = 0; i < NA; ++i) a[i] = 0.f;
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) a[j % F] = chunk_acc<FMT>(a[j % F], q.v[j], xv[s][j], sc[s]);
+      for (int j = 0; j < CPL; ++j) a[j % F] = chunk_acc<FMT>(a[j % F], q.v[j], xv[s][j], sc[s]);
 #pragma unroll
-        for (int h = F / 2; h >= 1; h >>= 1) {
+      for (int h = F / 2; h >= 1; h >>= 1) {
 #pragma unroll
-          for (int i = 0; i < h; ++i)
-            if (i + h < NA) a[i] = __fadd_rn(a[i], a[i + h]);
-        }
-        acc[s] = a[0];
+        for (int i = 0; i < h; ++i)
+          if (i + h < NA) a[i] = __fadd_rn(a[i], a[i + h]);
       }
+      acc[s] = a[0];
     }
-    group_reduce_n<P, U>(acc);
-#pragma unroll
-    for (int s = 0; s < U; ++s) {
-      const int c0 = base + s * VPW;
-      const float v = __shfl_sync(kFull, acc[s], ((lane - c0) * P) & 31);
-      if (lane >= c0 && lane < c0 + VPW) mine = v;
-    }
+    // candidate base + s*VPW + g is row s of group g
+    const float tot = group_reduce_spread<P, U>(acc);
+    const int rel = lane - base;
+    const bool mine_here = rel >= 0 && rel < VPW * U;
+    const float v = __shfl_sync(kFull, tot, mine_here ? spread_source<P, U>(rel / VPW, rel % VPW) : 0);
+    if (mine_here) mine = v;
   }
   return mine;
 }
@@ -602,12 +610,15 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
     if (lane == 0) S.bid[sel] = pid | kExpanded;
     sink.visit(lane, pid, pkey);
     st.hops += 1;
-    const int32_t *row = ix.graph + (int64_t)pid * ix.R;
+    const int64_t e0 = (int64_t)pid * ix.R;
     int rmin = cnt;
     for (int rb = 0; rb < ix.R; rb += 32) {
-      const int u = (rb + lane < ix.R) ? __ldg(row + rb + lane) : -1;
+      // the out-edge and its target's attribute word: the attribute is read
+      // whether or not the slot holds an edge, so both loads leave at once
+      const bool slot = rb + lane < ix.R;
+      const int u = slot ? __ldg(ix.graph + e0 + rb + lane) : -1;
       uint64_t aw = 0;
-      if (KeyFn::kEdgeAttr && u >= 0) aw = key1.edge_word(ix, (int64_t)pid * ix.R + rb + lane);
+      if (KeyFn::kEdgeAttr && slot) aw = key1.edge_word(ix, e0 + rb + lane);
       const bool full = (cnt == ls);
       const uint64_t tkey = full ? S.bkey[ls - 1] : kNoKey;
       const uint32_t tid = full ? (S.bid[ls - 1] & ~kExpanded) : kEmptySlot;
@@ -616,15 +627,17 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       // whose distance is computed need to be remembered
       uint32_t k1 = 0;
       bool cand = u >= 0;
-      if (cand) {
-        k1 = KeyFn::kEdgeAttr ? key1.from_word(aw) : key1(ix, u);
-        cand = KeyFn::kScalar || !(full && k1 > (uint32_t)(tkey >> 32));
+      if (KeyFn::kEdgeAttr) {
+        k1 = key1.from_word(aw);   // every lane (aw is 0 past the out-list): no branch
+      } else if (cand) {
+        k1 = key1(ix, u);
       }
+      cand = cand & (KeyFn::kScalar | !(full & (k1 > (uint32_t)(tkey >> 32))));
       bool keep = false;
       if (cand) keep = visit_insert(S.hash, hbits, (uint32_t)u);
-      st.seen += __popc(__ballot_sync(kFull, keep));
       const uint32_t km = __ballot_sync(kFull, keep);
       const int nc = __popc(km);
+      st.seen += nc;
       if (keep) {
         const int r = __popc(km & lanemask_lt());
         S.cid[r] = (uint32_t)u;
@@ -633,16 +646,15 @@ __device__ int greedy_search(const DevIndex &ix, const KeyFn &key1, const QChunk
       __syncwarp();
       if (nc == 0) continue;
       st.dcs += nc;
-      const float dist = candidate_distances<P, CPL, 4, FMT>(ix, q, S.cid, nc);
-      uint64_t ck = kNoKey;
-      uint32_t cv = kEmptySlot;
-      if (lane < nc) {
-        ck = key1.key(S.ck1[lane], dist);
-        cv = S.cid[lane];
-        if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
-      }
+      const float dist = candidate_distances<P, CPL, 4, FMT, prefetch_rows(FMT)>(ix, q, S.cid, nc);
+      // lanes past nc read stale slots of the 32-entry arrays and drop them
+      uint64_t ck = key1.key(S.ck1[lane], dist);
+      uint32_t cv = S.cid[lane];
+      const bool drop = (lane >= nc) | (full & !key_less(ck, cv, tkey, tid));
+      ck = drop ? kNoKey : ck;
+      cv = drop ? kEmptySlot : cv;
       int r0;
-      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0, S.rank);
+      cnt = merge_candidates<CAP>(S.bkey, S.bid, cnt, ls, ck, cv, r0);
       rmin = r0 < rmin ? r0 : rmin;
       if (POL == 2 && r0 < kq) last_change = st.hops;
     }

@@ -133,7 +133,7 @@ __device__ __forceinline__ int scan_merge(const DevIndex &ix, const QChunks<CPLF
     if (full && !key_less(ck, cv, tkey, tid)) { ck = kNoKey; cv = kEmptySlot; }
   }
   int r0;
-  return merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0, S.rank);
+  return merge_candidates<CAP, false>(S.bkey, S.bid, cnt, k, ck, cv, r0);
 }
 
 // Exact top-k over the ids of a sorted-column slice (the scan route of
@@ -294,8 +294,9 @@ __device__ void serve_query(const ServeArgs &a, const WarpSmem &S, const jag_fil
   write_answers(S, c2, 0, a.k, oid, od);
 }
 
+// Rows of one chunk per lane (d <= 128 fp32): 128 registers, 16 warps per SM.
 template <int CAP, int P, int CPL, int FMT, bool POL, int CPLF>
-__global__ void __launch_bounds__(kSearchWarps * 32)
+__global__ void __launch_bounds__(kSearchWarps * 32, CPLF == 1 ? 4 : 1)
 serve_kernel(const __grid_constant__ ServeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
