@@ -18,11 +18,11 @@
 //            acc_l + acc_(l xor o) for o = 16..1 (groups of P < 32 lanes only
 //            skip steps that would add exact zeros);
 //   merge    each surviving neighbour's position in the merged list is its
-//            rank in L (a fixed-step binary search) plus the number of
-//            smaller new keys; L is rebuilt from the back, 32 positions at a
-//            time, each lane fetching the entry that lands on its position;
-//            the best l_s are kept and a neighbour already in L (equal key
-//            and id) is dropped;
+//            rank in L (a fixed-step binary search on the keys, ties by id)
+//            plus the number of smaller new keys; L is rebuilt from the back,
+//            32 positions at a time, each lane fetching the entry that lands
+//            on its position; the best l_s are kept and a neighbour already
+//            in L (equal key and id) is dropped;
 // until every entry of L is expanded.
 //
 // The visited set may forget (a new id replaces the first of its two probe
@@ -100,22 +100,21 @@ __device__ __forceinline__ bool visit_insert(uint32_t *tab, int hbits, uint32_t 
   return fresh;
 }
 
-// Number of entries of the sorted list L[0..cnt) (cnt >= 1) that precede
-// (k, id): a binary search with a fixed number of steps and no branch, so
-// that every lane runs the same instructions.  TOP is the first step: CAP,
-// or CAP / 2 where the caller knows the key precedes L's last entry when L
-// holds CAP entries.  (A 4-way search, three probes a step, halves the chain
-// of dependent reads but was measured slower: it issues more instructions.)
+// Number of entries of the sorted list L[0..cnt) (cnt >= 1) whose 64-bit
+// key is below k: a binary search on the keys alone (one shared-memory read
+// a step), with a fixed number of steps and no branch, so that every lane
+// runs the same instructions.  TOP is the first step: CAP, or CAP / 2 where
+// the caller knows k precedes L's last entry when L holds CAP entries.  (A
+// 4-way search, three probes a step, halves the chain of dependent reads but
+// was measured slower: it issues more instructions.)
 template <int TOP>
-__device__ __forceinline__ int list_rank(const uint64_t *bkey, const uint32_t *bid, int cnt, uint64_t k,
-                                         uint32_t id) {
+__device__ __forceinline__ int key_lower_bound(const uint64_t *bkey, int cnt, uint64_t k) {
   int pos = 0;
 #pragma unroll
   for (int step = TOP; step >= 1; step >>= 1) {
     const int probe = pos + step;
     const int j = min(probe, cnt) - 1;
-    const bool before = (probe <= cnt) & key_less(bkey[j], bid[j] & ~kExpanded, k, id);
-    pos = before ? probe : pos;
+    pos = ((probe <= cnt) & (bkey[j] < k)) ? probe : pos;
   }
   return pos;
 }
@@ -140,11 +139,22 @@ __device__ __forceinline__ int merge_candidates(uint64_t *bkey, uint32_t *bid, i
   bool valid = ck != kNoKey;
   r0 = cnt;
   if (!__any_sync(kFull, valid)) return cnt;
-  // the graph search drops a key that follows a full list's last entry
-  // before the merge, so its ranks stay below CAP
-  const int rank = cnt == 0 ? 0 : list_rank<DEST ? CAP / 2 : CAP>(bkey, bid, cnt, ck, cv);
+  // rank in L under (key, id): the entries with a smaller key, then those
+  // with an equal key and a smaller id (equal keys are rare: one test).  The
+  // graph search drops a key that follows a full list's last entry before
+  // the merge, so its ranks stay below CAP.
+  int rank = cnt == 0 ? 0 : key_lower_bound<DEST ? CAP / 2 : CAP>(bkey, cnt, ck);
   {
-    const int rr = min(rank, cnt - 1);   // a key equal to L's entry at its rank is a repeat
+    int rr = min(rank, cnt - 1);
+    bool tie = (rank < cnt) & (bkey[rr] == ck) & ((bid[rr] & ~kExpanded) < cv);
+    if (__any_sync(kFull, tie)) {
+      while (tie) {
+        ++rank;
+        rr = min(rank, cnt - 1);
+        tie = (rank < cnt) & (bkey[rr] == ck) & ((bid[rr] & ~kExpanded) < cv);
+      }
+    }
+    // a key equal to L's entry at its rank, with the same id, is a repeat
     const bool rep = (rank < cnt) & (bkey[rr] == ck) & ((bid[rr] & ~kExpanded) == cv);
     valid = valid & (rank < ls) & !rep;
   }
