@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -108,8 +109,12 @@ struct jag_server {
     int32_t slot, nq;
     int64_t ids_off, dist_off;
     double submit;
+    uint64_t qbase;
   };
   std::unordered_map<uint64_t, Req> reqs;
+  // first query index of every uncollected request (the query map's live
+  // window starts at the smallest)
+  std::map<uint64_t, uint64_t> open_base;
   uint64_t next_ticket = 1, published = 0;
   int64_t held_queries = 0, launches = 0;
   bool launched = false;
@@ -159,7 +164,12 @@ Admit try_admit(jag_server *s, const float *queries, const jag_filter *filters, 
   const int64_t ob = align16((int64_t)nq * s->k * 4);
   const int64_t total = qb + fb + ab + 2 * ob;
   if (nq > s->qcap || total > s->arena_bytes || auxc * 8 > s->lut_bytes) return kNever;
-  if (s->free_slots.empty() || s->held_queries + nq > s->qcap) return kNoRoom;
+  // the query map is a ring over query indices: a new request's entries must
+  // not reach those of the oldest request still open, which may be claimed
+  // by a warp that has not read them yet
+  const uint64_t oldest = s->open_base.empty() ? s->published : s->open_base.begin()->first;
+  if (s->free_slots.empty() || s->held_queries + nq > s->qcap || s->published + nq - oldest > (uint64_t)s->qcap)
+    return kNoRoom;
   const uint64_t t = s->next_ticket;
   const int64_t off = s->arena_alloc.alloc(total, t);
   if (off < 0) return off == -2 ? kNever : kNoRoom;
@@ -203,7 +213,8 @@ Admit try_admit(jag_server *s, const float *queries, const jag_filter *filters, 
   s->ring[slot] = r;
   for (int32_t i = 0; i < nq; ++i) s->qmap[(s->published + i) % (uint64_t)s->qcap] = (uint32_t)slot;
   s->held_queries += nq;
-  s->reqs[t] = {slot, nq, r.ids_off, r.dist_off, submit};
+  s->reqs[t] = {slot, nq, r.ids_off, r.dist_off, submit, s->published};
+  s->open_base[s->published] = t;
   s->published += nq;
   __atomic_store_n(&s->ctl->published, (unsigned long long)s->published, __ATOMIC_RELEASE);
   *ticket = t;
@@ -232,6 +243,7 @@ void collect(jag_server *s, uint64_t ticket, int32_t *ids, float *dist, jag_serv
   s->lut_alloc.release(ticket);
   s->free_slots.push_back(r.slot);
   s->held_queries -= r.nq;
+  s->open_base.erase(r.qbase);
   s->reqs.erase(ticket);
 }
 
@@ -338,6 +350,7 @@ JAG_API jag_status jag_serve_start(jag_index *idx, const jag_serve_params *p, ja
   g.done_cnt = reinterpret_cast<int32_t *>(dv + d_cnt);
   g.req_status = reinterpret_cast<uint32_t *>(dv + d_status);
   g.t_first = reinterpret_cast<unsigned long long *>(dv + d_first);
+  g.nslots = s->slots;
   g.idle_ns = (unsigned long long)((p->idle_exit_s > 0.0 ? p->idle_exit_s : 1.0) * 1e9);
   g.has_policy = p->policy && p->policy->mode == JAG_POLICY_LEARNED ? 1 : 0;
   if (g.has_policy) g.pol = *p->policy;

@@ -50,6 +50,8 @@ struct ServeCtl {
 struct ServeDev {
   unsigned long long claimed;        // queries claimed so far
   unsigned long long queries_done;
+  unsigned long long pub_seen;       // the largest published count a warp has read from the host
+  unsigned long long bad_claims;     // claimed queries whose map entry named another request (skipped)
 };
 
 struct ServeArgs {
@@ -70,6 +72,7 @@ struct ServeArgs {
   unsigned long long idle_ns;
   jag_policy pol;
   int has_policy;
+  int nslots;                       // request slots (ring, done, done_cnt, ... entries)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -94,22 +97,51 @@ __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned l
   asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Claim the next published query (lane 0 only); -1: exit (stop, or idle for
-// longer than idle_ns).  The compare-and-swap loop ends because every failed
-// attempt means another warp advanced the counter towards `published`.
-__device__ inline long long serve_claim(const ServeArgs &a) {
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void max_release_gpu(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Claim a run of published queries [*c0, *c0 + n) (lane 0 only); returns n,
+// 0 to exit (stop, or idle for longer than idle_ns).  One compare-and-swap
+// takes a share of the backlog (backlog / warps, 1..8 queries): under
+// contention one compare-and-swap succeeds per round trip to L2, which
+// would otherwise cap the loop at a few million queries a second.  The
+// host's published count is read (acquire, system scope) only when the
+// claims have caught up with the largest count any warp has seen; that count
+// is passed on in device memory with release / acquire at GPU scope, which
+// carries the host's writes along.  The compare-and-swap loop ends because
+// every failed attempt means another warp advanced the counter.
+__device__ inline int serve_claim(const ServeArgs &a, unsigned long long warps, unsigned long long *c0) {
   const unsigned long long t0 = global_ns();
   unsigned int nap = 64;
   for (;;) {
-    const unsigned long long p = ld_acquire_sys(&a.ctl->published);
+    unsigned long long p = ld_acquire_gpu(&a.dev->pub_seen);
     unsigned long long c = atomicAdd(&a.dev->claimed, 0ull);
+    if (c >= p) {
+      const unsigned long long h = ld_acquire_sys(&a.ctl->published);
+      if (h > p) {
+        max_release_gpu(&a.dev->pub_seen, h);
+        p = h;
+      }
+    }
     while (c < p) {
-      const unsigned long long prev = atomicCAS(&a.dev->claimed, c, c + 1);
-      if (prev == c) return (long long)c;
+      unsigned long long n = (p - c) / warps;
+      n = n < 1 ? 1 : (n > 8 ? 8 : n);
+      const unsigned long long prev = atomicCAS(&a.dev->claimed, c, c + n);
+      if (prev == c) {
+        *c0 = c;
+        return (int)n;
+      }
       c = prev;
     }
-    if (ld_volatile_u32(&a.ctl->stop)) return -1;
-    if (global_ns() - t0 > a.idle_ns) return -1;
+    if (ld_volatile_u32(&a.ctl->stop)) return 0;
+    if (global_ns() - t0 > a.idle_ns) return 0;
     __nanosleep(nap);
     if (nap < 8192) nap <<= 1;
   }
@@ -304,14 +336,26 @@ serve_kernel(const __grid_constant__ ServeArgs a) {
   const size_t wbytes = warp_smem_bytes(lcap, a.hbits);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, a.hbits);
-  for (;;) {
-    long long c = 0;
-    if (lane == 0) c = serve_claim(a);
-    c = __shfl_sync(kFull, c, 0);
-    if (c < 0) return;
+  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  unsigned long long c = 0;
+  int have = 0;   // queries of the current claim not yet answered, from c on
+  for (;; ++c, --have) {
+    if (have == 0) {
+      unsigned long long c0 = 0;
+      if (lane == 0) have = serve_claim(a, warps, &c0);
+      have = __shfl_sync(kFull, have, 0);
+      c = __shfl_sync(kFull, c0, 0);
+      if (have == 0) return;
+    }
     const uint32_t slot = a.qmap[(unsigned long long)c % (unsigned long long)a.qcap];
-    const ServeReq rq = a.ring[slot];
+    const ServeReq rq = a.ring[slot < (uint32_t)a.nslots ? slot : 0u];
     const int64_t i = c - rq.qbase;
+    // cannot happen while the host keeps the map's window; never read out of range
+    if (slot >= (uint32_t)a.nslots || i < 0 || i >= rq.nq) {
+      if (lane == 0) atomicAdd(&a.dev->bad_claims, 1ull);
+      __syncwarp();
+      continue;
+    }
     if (i == 0 && lane == 0) a.t_first[slot] = global_ns();
     const jag_filter f = reinterpret_cast<const jag_filter *>(a.arena + rq.f_off)[i];
     const float *qv = reinterpret_cast<const float *>(a.arena + rq.q_off) + i * a.d;
