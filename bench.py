@@ -21,7 +21,8 @@ The same JSON line also carries the other forms: BF16 / FP8 rows and the
 learned stop policy on the label workload; the learned beam / stop network
 on the mixed range / boolean workload (two graphs, 100,000 training
 queries); the precision form on subset filters (d = 100, fp32 / BF16 / FP8
-rows); the 10M-point BF16 serving form with the serve loop's p50 / p99; the
+rows); the 10M-point BF16 serving form, indexed at R = 32 and R = 64, with
+the serve loop's p50 / p99; the
 serve loop on the label index; and the oracle on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -1130,29 +1131,41 @@ def run_serve_large(args):
 def measure_large(args, local):
     """The serving form at its own scale: N = 10M, d = 100, BF16 rows (fp32
     re-rank), float attribute U[0,1), range filters of width log-uniform in
-    [1e-4, 1], R = 32.  Picks the smallest beam with recall@10 >= 0.95 in
-    every band on a ground-truth sample (else the largest beam, and says so),
-    times the batch search at that beam and at 256 (the serve loop's largest),
-    then replays Poisson traffic through the serve loop at beam <= 256."""
-    import torch
+    [1e-4, 1].  The data are generated once and indexed at each degree of
+    --large-r: R = 32 (the form's stated degree) and R = 64.  For each, the
+    smallest beam with recall@10 >= 0.95 in every band on a ground-truth
+    sample (else the largest beam, and says so), the batch search timed at
+    that beam and at 256 (the serve loop's largest), then Poisson traffic
+    replayed through the serve loop at beam <= 256.  Returns the R = 32
+    result, with the others under "other_degrees"."""
     from paper_2602_10258_gb300 import datagen as D
-    from paper_2602_10258_gb300 import jag
-    dev = torch.device("cuda", local)
     t0 = time.time()
     w = D.make_range_f32(n=args.large_n, d=100, nq=10000, seed=args.seed)
     gen_s = time.time() - t0
-    t0 = time.time()
-    thr = tuple(int(v) for v in args.large_thresholds.split(","))
-    idx = jag.Index.from_workload(w, R=R, l_b=args.large_lb, alpha=args.large_alpha, thresholds=thr,
-                                  storage=jag.JAG_VEC_BF16, device=local)
-    build_s = time.time() - t0
-    info = idx.info()
-    log("large: data %.1f s, build %.1f s (GPU %.1f s), %.2f GB on the device" % (
-        gen_s, build_s, info["build_seconds"], info["device_bytes"] / 1e9))
     srt = np.sort(w.attr_f32)
     fl = D.filter_fields(w.filters)
     sel = (np.searchsorted(srt, fl["f_hi"], "right") - np.searchsorted(srt, fl["f_lo"], "left")) / w.n
     band = band_of(sel)
+    log("large: data %.1f s" % gen_s)
+    outs = [measure_large_at(args, local, w, band, int(r)) for r in args.large_r.split(",")]
+    out = outs[0]
+    if len(outs) > 1:
+        out["other_degrees"] = {"R%d" % o["config"]["R"]: o for o in outs[1:]}
+    return out
+
+
+def measure_large_at(args, local, w, band, degree):
+    import torch
+    from paper_2602_10258_gb300 import jag
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    thr = tuple(int(v) for v in args.large_thresholds.split(","))
+    idx = jag.Index.from_workload(w, R=degree, l_b=args.large_lb, alpha=args.large_alpha, thresholds=thr,
+                                  storage=jag.JAG_VEC_BF16, device=local)
+    build_s = time.time() - t0
+    info = idx.info()
+    log("large R=%d: build %.1f s (GPU %.1f s), %.2f GB on the device" % (
+        degree, build_s, info["build_seconds"], info["device_bytes"] / 1e9))
     nq = len(w.q)
     q = torch.from_numpy(w.q).to(dev)
     ft = jag.filters_to_device(w.filters, dev)
@@ -1175,7 +1188,7 @@ def measure_large(args, local):
         per = {name: float(np.mean(rec[(band[:ns] == j) & ~np.isnan(rec)])) for j, (_, _, name) in enumerate(BANDS)
                if ((band[:ns] == j) & ~np.isnan(rec)).any()}
         sweep[beam] = {k: round(v, 4) for k, v in per.items()}
-        log("large beam %d: %s" % (beam, sweep[beam]))
+        log("large R=%d beam %d: %s" % (degree, beam, sweep[beam]))
         if all(v >= 0.95 for v in per.values()):
             chosen, per_chosen = beam, per
             break
@@ -1208,20 +1221,21 @@ def measure_large(args, local):
     serving["beam"] = serve_beam
     serving["recall_at_beam"] = sweep.get(serve_beam)
     idx.close()
-    out = {"metric": METRIC, "unit": "queries/s", "dtype": "bf16 rows, f32 re-rank",
-           "data": "synthetic",
-           "config": {"workload": "float range, width log-uniform 1e-4..1, N=%d d=100 GMM-200, 10000 queries, "
-                                  "k=10, R=%d" % (w.n, R), "beam": chosen, "recall_0.95_met": met, "s0": S0,
-                      "scan_cap": SCAN_CAP,
-                      "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.2f" % (args.large_lb, list(thr),
-                                                                               args.large_alpha),
-                      "build_seconds": round(build_s, 1), "gpu_build_seconds": round(info["build_seconds"], 1),
-                      "index_device_bytes": info["device_bytes"], "ground_truth_sample": ns,
-                      "ground_truth_seconds": round(gt_s, 1), "beam_sweep": {str(b): v for b, v in sweep.items()}},
-           "batch": {"qps": round(qps, 1), "ms_per_step": round(ms, 3), "recall": per_chosen,
-                     "beam_256_qps": round(nq / (ms_serve_beam / 1000.0), 1)},
-           "serving": serving}
-    return out
+    del flush, ids, dd, q
+    torch.cuda.empty_cache()
+    return {"metric": METRIC, "unit": "queries/s", "dtype": "bf16 rows, f32 re-rank",
+            "data": "synthetic",
+            "config": {"workload": "float range, width log-uniform 1e-4..1, N=%d d=100 GMM-200, 10000 queries, "
+                                   "k=10, R=%d" % (w.n, degree), "R": degree, "beam": chosen, "recall_0.95_met": met,
+                       "s0": S0, "scan_cap": SCAN_CAP,
+                       "build": "GPU JAG build, l_b=%d, T=%s%%, alpha=%.2f" % (args.large_lb, list(thr),
+                                                                                args.large_alpha),
+                       "build_seconds": round(build_s, 1), "gpu_build_seconds": round(info["build_seconds"], 1),
+                       "index_device_bytes": info["device_bytes"], "ground_truth_sample": ns,
+                       "ground_truth_seconds": round(gt_s, 1), "beam_sweep": {str(b): v for b, v in sweep.items()}},
+            "batch": {"qps": round(qps, 1), "ms_per_step": round(ms, 3), "recall": per_chosen,
+                      "beam_256_qps": round(nq / (ms_serve_beam / 1000.0), 1)},
+            "serving": serving}
 
 
 def run_profile(args):
@@ -1280,6 +1294,7 @@ def main():
     ap.add_argument("--large-thresholds", default="100,10,0", help="threshold percentiles of the large form's build")
     ap.add_argument("--large-lb", type=int, default=128, help="build beam of the large form")
     ap.add_argument("--large-alpha", type=float, default=ALPHA, help="pruning alpha of the large form")
+    ap.add_argument("--large-r", default="32,64", help="graph degrees of the large form (the first is reported)")
     ap.add_argument("--beam", type=int, default=192)
     ap.add_argument("--profile-workload", default="label", choices=["label", "subset"],
                     help="workload of the --profile run: the label workload or the precision form's subset one")

@@ -489,7 +489,9 @@ JAG_API jag_status jag_serve_replay(jag_server *s, int64_t n_req, const double *
     bool progress = false;
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      // arrivals that are due, in order, while there is room
+      // arrivals that are due, in order, while there is room (the loop is
+      // checked once for the whole group)
+      bool admitted = false;
       while (next < n_req && now >= start + arrival_s[next]) {
         uint64_t t;
         const int64_t row = first[next];
@@ -499,9 +501,10 @@ JAG_API jag_status jag_serve_replay(jag_server *s, int64_t n_req, const double *
         if (a == kNoRoom) break;
         open.push_back({next, t, s->reqs[t].slot});
         ++next;
-        progress = true;
-        if (jag_status st = ensure_running(s)) return st;
+        progress = admitted = true;
       }
+      if (admitted)
+        if (jag_status st = ensure_running(s)) return st;
       // completions, in any order
       for (auto it = open.begin(); it != open.end();) {
         if (!is_done(s, it->slot, it->ticket)) { ++it; continue; }
