@@ -152,7 +152,7 @@ weights_kernel(DevIndex ix, int S, uint64_t seed, int nW, Mult mult, uint32_t *w
         sa[warp][i] = ix.dist_a == JAG_F_RANGE_F32 ? u2f(da) : __uint2float_rn(da);
       }
       __syncwarp();
-      const float dist = candidate_distances<P, CPL>(ix, q, sid[warp], nc);
+      const float dist = candidate_distances<P, CPL, 4, JAG_VEC_F32, true>(ix, q, sid[warp], nc);
       if (lane < nc) sd[warp][i0 + lane] = dist;
       __syncwarp();
     }
@@ -349,7 +349,7 @@ __device__ void joint_prune(const DevIndex &ix, int64_t p, const PruneSmem &S, i
         load_point<P, CPL>(ix.x + (int64_t)v * ix.xs, (int)ix.xs, xv);
         for (int b0 = 0; b0 < nb && keep; b0 += 32) {
           const int m = min(32, nb - b0);
-          const float duv = candidate_distances<P, CPL>(ix, xv, S.bucket + b0, m);
+          const float duv = candidate_distances<P, CPL, 4, JAG_VEC_F32, true>(ix, xv, S.bucket + b0, m);
           const bool bad = lane < m && !(__fmul_rn(alpha2, duv) > dpv);
           if (__any_sync(kFull, bad)) keep = false;
         }
@@ -436,7 +436,7 @@ prune_insert_kernel(DevIndex ix, int32_t *graph, int64_t pos0, int64_t nb, int n
       load_point<P, CPL>(ix.x + p * ix.xs, (int)ix.xs, xp);
       for (int b = 0; b < w; b += 32) {
         const int m = min(32, w - b);
-        const float dv = candidate_distances<P, CPL>(ix, xp, S.cid + b, m);
+        const float dv = candidate_distances<P, CPL, 4, JAG_VEC_F32, true>(ix, xp, S.cid + b, m);
         if (lane < m) S.cdist[b + lane] = dv;
       }
       __syncwarp();
@@ -533,7 +533,7 @@ edge_apply_kernel(DevIndex ix, int32_t *graph, int64_t cap_targets, int nT, cons
       load_point<P, CPL>(ix.x + (int64_t)v * ix.xs, (int)ix.xs, xv);
       for (int b = 0; b < nc; b += 32) {
         const int m = min(32, nc - b);
-        const float dv = candidate_distances<P, CPL>(ix, xv, S.cid + b, m);
+        const float dv = candidate_distances<P, CPL, 4, JAG_VEC_F32, true>(ix, xv, S.cid + b, m);
         if (lane < m) S.cdist[b + lane] = dv;
       }
       __syncwarp();

@@ -471,7 +471,7 @@ brute_tile_kernel(DevIndex ix, const float *queries, int d, const jag_filter *fi
     const bool full = cnt == k;
     const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
     const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
-    const float dist = candidate_distances<P, CPL>(ix, q, S.cid, nc);
+    const float dist = candidate_distances<P, CPL, 4, JAG_VEC_F32, true>(ix, q, S.cid, nc);
     uint64_t ck = kNoKey;
     uint32_t cv = kEmptySlot;
     if (lane < nc) {
@@ -546,7 +546,7 @@ rerank_kernel(DevIndex ix, const float *queries, int d, const QueryPlan *plans, 
     const bool full = cnt == k;
     const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
     const uint32_t tid = full ? S.bid[k - 1] : kEmptySlot;
-    const float dist = candidate_distances<P, CPL, 4, JAG_VEC_F32>(ix, q, S.cid, nc);
+    const float dist = candidate_distances<P, CPL, 4, JAG_VEC_F32, true>(ix, q, S.cid, nc);
     uint64_t ck = kNoKey;
     uint32_t cv = kEmptySlot;
     if (lane < nc) {

@@ -36,7 +36,8 @@
 namespace jag {
 
 // Whether the graph search asks L2 for the rows of a hop's candidates past
-// its first batch of loads before it starts the batches.  Requesting the
+// its first batch of loads before it starts the batches (the exact scans,
+// re-ranks and the build always do: their batches hold up to 32 rows).  Requesting the
 // out-list of the likely next vertex (the second unexpanded entry of L) was
 // measured slower for every format.
 __host__ __device__ constexpr bool prefetch_rows(int FMT) { return FMT != JAG_VEC_FP8; }

@@ -107,22 +107,33 @@ __device__ __forceinline__ void max_release_gpu(unsigned long long *p, unsigned 
   asm volatile("red.release.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Claim a run of published queries [*c0, *c0 + n) (lane 0 only); returns n,
-// 0 to exit (stop, or idle for longer than idle_ns).  One compare-and-swap
-// takes a share of the backlog (backlog / warps, 1..8 queries): under
-// contention one compare-and-swap succeeds per round trip to L2, which
-// would otherwise cap the loop at a few million queries a second.  The
-// host's published count is read (acquire, system scope) only when the
-// claims have caught up with the largest count any warp has seen; that count
-// is passed on in device memory with release / acquire at GPU scope, which
-// carries the host's writes along.  The compare-and-swap loop ends because
-// every failed attempt means another warp advanced the counter.
-__device__ inline int serve_claim(const ServeArgs &a, unsigned long long warps, unsigned long long *c0) {
-  const unsigned long long t0 = global_ns();
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Claim the next query (lane 0 only): returns 1 with its index in *c0, 0 to
+// exit (stop, or idle for longer than idle_ns).
+//
+// A claim is a ticket from one atomicAdd on the claim counter, taken once
+// the warp has seen published work nobody claimed; with many warps some
+// tickets run ahead of what is published, and their holders wait, in ticket
+// order, for the host to publish them.  (A compare-and-swap claim never runs
+// ahead, but under contention only one succeeds per round trip to L2, which
+// caps dispatch near two million queries a second.)  The holder of the
+// oldest unpublished ticket reads the host's published count (acquire,
+// system scope) and passes it on in device memory (release / acquire, GPU
+// scope), which carries the host's writes along; the others read only that
+// copy.  A holder idle for idle_ns gives its ticket back when it is the
+// newest one (one compare-and-swap), so tickets return in the reverse order
+// of their claims and none is lost or handed out twice.
+__device__ inline int serve_claim(const ServeArgs &a, unsigned long long *c0) {
+  unsigned long long t0 = global_ns();
   unsigned int nap = 64;
-  for (;;) {
+  for (;;) {   // no ticket yet
     unsigned long long p = ld_acquire_gpu(&a.dev->pub_seen);
-    unsigned long long c = atomicAdd(&a.dev->claimed, 0ull);
+    const unsigned long long c = ld_relaxed_gpu(&a.dev->claimed);
     if (c >= p) {
       const unsigned long long h = ld_acquire_sys(&a.ctl->published);
       if (h > p) {
@@ -130,20 +141,32 @@ __device__ inline int serve_claim(const ServeArgs &a, unsigned long long warps, 
         p = h;
       }
     }
-    while (c < p) {
-      unsigned long long n = (p - c) / warps;
-      n = n < 1 ? 1 : (n > 8 ? 8 : n);
-      const unsigned long long prev = atomicCAS(&a.dev->claimed, c, c + n);
-      if (prev == c) {
-        *c0 = c;
-        return (int)n;
-      }
-      c = prev;
-    }
+    if (c < p) break;
     if (ld_volatile_u32(&a.ctl->stop)) return 0;
     if (global_ns() - t0 > a.idle_ns) return 0;
     __nanosleep(nap);
     if (nap < 8192) nap <<= 1;
+  }
+  const unsigned long long t = atomicAdd(&a.dev->claimed, 1ull);
+  t0 = global_ns();
+  nap = 32;
+  for (;;) {   // holding ticket t
+    const unsigned long long p = ld_acquire_gpu(&a.dev->pub_seen);
+    if (t < p) {
+      *c0 = t;
+      return 1;
+    }
+    if (t == p) {   // the oldest unpublished ticket
+      const unsigned long long h = ld_acquire_sys(&a.ctl->published);
+      if (h > p) {
+        max_release_gpu(&a.dev->pub_seen, h);
+        continue;
+      }
+    }
+    if (ld_volatile_u32(&a.ctl->stop)) return 0;
+    if (global_ns() - t0 > a.idle_ns && atomicCAS(&a.dev->claimed, t + 1, t) == t + 1) return 0;
+    __nanosleep(nap);
+    if (nap < 4096) nap <<= 1;
   }
 }
 
@@ -156,7 +179,7 @@ __device__ __forceinline__ int scan_merge(const DevIndex &ix, const QChunks<CPLF
   const bool full = cnt == k;
   const uint64_t tkey = full ? S.bkey[k - 1] : kNoKey;
   const uint32_t tid = full ? (S.bid[k - 1] & ~kExpanded) : kEmptySlot;
-  const float dist = candidate_distances<PF, CPLF, 4, JAG_VEC_F32>(ix, qf, ids, nc);
+  const float dist = candidate_distances<PF, CPLF, 4, JAG_VEC_F32, true>(ix, qf, ids, nc);
   uint64_t ck = kNoKey;
   uint32_t cv = kEmptySlot;
   if (lane < nc) {
@@ -336,17 +359,13 @@ serve_kernel(const __grid_constant__ ServeArgs a) {
   const size_t wbytes = warp_smem_bytes(lcap, a.hbits);
   uint8_t *wb = smem + warp * wbytes;
   const WarpSmem S = carve_warp_smem(wb, lcap, a.hbits);
-  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-  unsigned long long c = 0;
-  int have = 0;   // queries of the current claim not yet answered, from c on
-  for (;; ++c, --have) {
-    if (have == 0) {
-      unsigned long long c0 = 0;
-      if (lane == 0) have = serve_claim(a, warps, &c0);
-      have = __shfl_sync(kFull, have, 0);
-      c = __shfl_sync(kFull, c0, 0);
-      if (have == 0) return;
-    }
+  for (;;) {
+    unsigned long long c = 0;
+    int got = 0;
+    if (lane == 0) got = serve_claim(a, &c);
+    got = __shfl_sync(kFull, got, 0);
+    c = __shfl_sync(kFull, c, 0);
+    if (!got) return;
     const uint32_t slot = a.qmap[(unsigned long long)c % (unsigned long long)a.qcap];
     const ServeReq rq = a.ring[slot < (uint32_t)a.nslots ? slot : 0u];
     const int64_t i = c - rq.qbase;
