@@ -701,7 +701,8 @@ def measure_mixed(args, local, flush, stream):
     the smallest beam with recall@10 >= 0.95 in every band of its queries)
     against BF16 rows with the learned beam / stop network, trained on the
     GPU on traces of 100,000 training queries labelled with the smallest
-    ladder beam reaching recall 0.95."""
+    ladder beam reaching recall 0.95; the same networks also run on the fp32
+    rows."""
     import torch
     from paper_2602_10258_gb300 import datagen as D
     from paper_2602_10258_gb300 import jag
@@ -848,6 +849,32 @@ def measure_mixed(args, local, flush, stream):
     forms["bf16_learned"] = learned
     log("mixed learned: %s" % {k: v for k, v in learned.items() if k in ("label_shift", "tau", "stop_scale", "qps",
                                                                        "recall", "mean_hops_graph_route")})
+    # the same networks on the fp32 rows, at the plain fp32 form's beams: the
+    # fastest candidate that keeps recall >= 0.95 in every band
+    base32 = (forms["plain_fp32"]["beam_range"], forms["plain_fp32"]["beam_bool"])
+    best32 = None
+    for shift, tau, scale, _, _, _ in cands:
+        pol = jag.Policy.learned(nets[shift][0], ladder=MIXED_LADDER, h0=MIXED_H0, tau=tau, stop_scale=scale)
+        per, cnt = evaluate(mix32, base32, pol)
+        if not all(v >= 0.95 for v in per.values()):
+            continue
+        ms = timed(mix32, base32, pol, steps)
+        if best32 is None or ms < best32[0]:
+            best32 = (ms, shift, tau, scale, per, cnt)
+    if best32 is None:
+        forms["fp32_learned"] = {"qps": None, "note": "no candidate kept recall 0.95 in every band on fp32 rows"}
+    else:
+        ms, shift, tau, scale, per, cnt = best32
+        gbytes = mixed_graph_bytes(cnt[hb.rows[0]], 512, 4) + mixed_graph_bytes(cnt[hb.rows[1]], 512, 8)
+        forms["fp32_learned"] = {"base_beam_range": base32[0], "base_beam_bool": base32[1], "h0": MIXED_H0,
+                                 "label_shift": shift, "tau": tau, "stop_scale": scale,
+                                 "networks": "trained on the BF16 traces", "qps": round(hb.n / (ms / 1e3), 1),
+                                 "ms_per_step": round(ms, 4), "recall": per,
+                                 "mean_hops_graph_route": round(float(cnt[cnt[:, 3] == 0, 0].mean()), 1),
+                                 "gather_bytes_per_step": gbytes,
+                                 "gather_frac_of_hbm": round(gbytes / (ms / 1e3) / 1e9 / measured_peaks()[0], 4)}
+    log("mixed learned fp32: %s" % {k: v for k, v in forms["fp32_learned"].items()
+                                    if k in ("label_shift", "tau", "stop_scale", "qps", "recall")})
     out["forms"] = forms
     out["prep_seconds"] = round(prep_s, 1)
     mix32.close()
