@@ -112,6 +112,28 @@ def test_replay_answers_and_latencies(case):
     assert (lat > 0).all() and (dev >= 0).all() and (dev <= lat + 1e-3).all()
 
 
+def test_small_query_map_with_out_of_order_completion(case):
+    # a 128-entry query map, a burst of requests mixing exact scans (quick)
+    # and graph searches (slow): requests complete out of order, admission
+    # waits for the map's window, and most warps hold tickets ahead of the
+    # published count; every answer must still be the batch path's
+    w, ix = case
+    bi, bd, _ = _batch_answers(ix, w, 600)
+    rng = np.random.default_rng(11)
+    n_req = 300
+    sizes = rng.integers(1, 49, n_req).astype(np.int32)
+    first = np.array([rng.integers(0, len(w.q) - s + 1) for s in sizes], np.int64)
+    arrival = np.cumsum(rng.exponential(2e-6, n_req))
+    srv = jag.Server(ix, K, BEAM, s0=600, max_queries=128)
+    ids, dist, lat, dev = srv.replay(arrival, sizes, first, w.q, w.filters, w.aux, timeout_s=60.0)
+    info = srv.info()
+    srv.stop()
+    assert info["queries_done"] == int(sizes.sum())
+    for f, sz in zip(first, sizes):
+        assert np.array_equal(ids[f:f + sz], bi[f:f + sz])
+        assert np.array_equal(dist[f:f + sz].view(np.uint32), bd[f:f + sz].view(np.uint32))
+
+
 def test_admission_timeout_and_unknown_ticket(case):
     w, ix = case
     srv = jag.Server(ix, K, BEAM, max_queries=64)
