@@ -414,8 +414,11 @@ struct PolicyOut {
 
 // Features of the list L[0..cnt) after the decision hop and the policy's
 // beam / stop (every lane returns the same).  hbuf: 64 floats of the warp.
-__device__ __noinline__ static PolicyOut policy_decide(const jag_policy &pol, const WarpSmem &S, float *hbuf, int cnt, int k,
-                                   int64_t est, int32_t kind, int fixed, float *feat_out, const int32_t *forced_q) {
+// Inlined: with the lean search loop the policy kernels fit their register
+// budget without a call.
+__device__ __forceinline__ static PolicyOut policy_decide(const jag_policy &pol, const WarpSmem &S, float *hbuf,
+                                                          int cnt, int k, int64_t est, int32_t kind, int fixed,
+                                                          float *feat_out, const int32_t *forced_q) {
   const int lane = threadIdx.x & 31;
   // passing prefix and first unexpanded entry
   int np = cnt;
