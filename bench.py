@@ -990,7 +990,7 @@ def measure_subset(args, local, flush, stream):
     return out
 
 
-def serve_saturation(jag, idx, w, beam, batch_qps, n_req=2000, offered=(0.6, 0.8, 1.0)):
+def serve_saturation(jag, idx, w, beam, batch_qps, n_req=2000, offered=(0.6, 1.0, 1.5)):
     """Saturated throughput of the serve loop: the largest QPS it achieves
     under Poisson arrivals of the request mix (sizes uniform in 1..256
     queries) offered at the given fractions of the batch path's QPS."""
