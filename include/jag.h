@@ -330,7 +330,9 @@ typedef struct jag_serve_params {
   int32_t hash_bits;           /* as jag_search_args.hash_bits                 */
   int32_t max_requests;        /* ring slots (admitted, not yet collected);
                                   0 = 1024, at most 65536                      */
-  int64_t max_queries;         /* queries admitted at once; 0 = 65536          */
+  int64_t max_queries;         /* queries admitted at once, counted from the
+                                  first query of the oldest uncollected
+                                  request to the last published; 0 = 65536   */
   int64_t arena_bytes;         /* host arena for inputs / outputs; 0 = enough
                                   for max_queries queries with 64 bytes of
                                   truth tables each                            */

@@ -1,15 +1,17 @@
 // Device-resident request loop (serving with continuous batching).
 //
 // A persistent kernel: each warp repeatedly claims the next published query
-// (a global index over all requests, in publication order), finds its
+// (a global index over all requests, in publication order, handed out as
+// tickets; see serve_claim), finds its
 // request through the query map, answers it exactly as the batched search
 // does (the plan of plan_query, then the exact scan or GreedySearch of
 // Algorithm 1 with D_F, then the fp32 re-rank for BF16 / FP8 rows) and writes
 // the answers straight into the request's output rows in mapped host memory.
 // The warp that finishes a request's last query writes its completion record.
 // Requests, their inputs and outputs live in pinned host memory the host
-// writes and reads directly; the only device-side state is the claim counter
-// and per-slot completion counters.
+// writes and reads directly; the only device-side state is the claim counter,
+// the published count last read from the host, and per-slot completion
+// counters.
 //
 // Every wait is bounded: a warp with nothing to claim backs off with
 // __nanosleep and exits after idle_ns without work or once the host sets
