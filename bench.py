@@ -179,17 +179,24 @@ def profile_traffic(src_hash):
 
 
 # Sources the query path's kernels (graph search, scan, preparation) are
-# compiled from; a profile summary is valid while they are unchanged.
+# compiled from; a profile summary is valid while their code is unchanged
+# (the hash skips comments).
 QUERY_SOURCES = ["paper_2602_10258_gb300/csrc/" + f for f in (
     "jag_internal.cuh", "launch.h", "launch_util.cuh", "plan.cuh", "query_graph.cuh", "search.cu",
     "search_core.cuh", "search_f32.cu")] + ["include/jag.h"]
+
+
+def strip_comments(src):
+    """C / C++ source without its comments (string literals kept)."""
+    return re.sub(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"',
+                  lambda m: m.group(0) if m.group(0).startswith('"') else " ", src, flags=re.S)
 
 
 def kernel_source_hash():
     import hashlib
     hs = hashlib.sha256()
     for f in QUERY_SOURCES:
-        hs.update(open(os.path.join(ROOT, f), "rb").read())
+        hs.update(strip_comments(open(os.path.join(ROOT, f), encoding="utf-8").read()).encode())
     return hs.hexdigest()[:16]
 
 
