@@ -193,10 +193,13 @@ def strip_comments(src):
 
 
 def kernel_source_hash():
+    """sha256 (16 hex digits) of the query path's sources with comments
+    removed and runs of white space made one space."""
     import hashlib
     hs = hashlib.sha256()
     for f in QUERY_SOURCES:
-        hs.update(strip_comments(open(os.path.join(ROOT, f), encoding="utf-8").read()).encode())
+        code = strip_comments(open(os.path.join(ROOT, f), encoding="utf-8").read())
+        hs.update(re.sub(r"\s+", " ", code).strip().encode())
     return hs.hexdigest()[:16]
 
 
