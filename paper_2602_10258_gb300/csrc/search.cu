@@ -120,17 +120,18 @@ __global__ void list_leader_kernel(QueryPlan *plans, const jag_filter *filters, 
   else leaders[nq - 1 - (int64_t)atomicAdd(&nlead[1], 1ull)] = (int32_t)qi;
 }
 
-// K2a: one CTA per subset leader walks the posting list of its rarest
-// required bit and keeps the points that hold every required bit; each lane
+// K2a: kPostParts CTAs per subset leader walk the posting list of its rarest
+// required bit, one part each, and keep the points that hold every required
+// bit (in any order: the scan's answers do not depend on it); each lane
 // keeps kPostUnroll loads in flight.  Past cap points the list is full and
 // the count only has to exceed cap (the query then goes to the graph).
 constexpr int kPostWarps = 8;
 constexpr int kPostUnroll = 4;
+constexpr int kPostParts = 8;   // CTAs per leader, each over one part of its posting list
 
 __global__ void __launch_bounds__(kPostWarps * 32)
 gather_postings_kernel(DevIndex ix, const jag_filter *filters, const int32_t *leaders,
                        const unsigned long long *nlead, int64_t cap, int32_t *lists, int32_t *counts) {
-  __shared__ int s_cnt;
   const int64_t w = blockIdx.x;
   if (w >= (int64_t)nlead[0]) return;
   const int lane = threadIdx.x & 31;
@@ -143,12 +144,14 @@ gather_postings_kernel(DevIndex ix, const jag_filter *filters, const int32_t *le
     const int64_t len = ix.bit_off[j + 1] - ix.bit_off[j];
     if (len < best) { best = len; jb = j; }
   }
-  if (threadIdx.x == 0) s_cnt = 0;
-  __syncthreads();
-  const int64_t b0 = ix.bit_off[jb], b1 = ix.bit_off[jb + 1];
+  // this CTA's part of the list; positions come from the leader's count
+  // (zeroed by the preparation kernel), so the parts fill one list
+  const int64_t l0 = ix.bit_off[jb], len = ix.bit_off[jb + 1] - l0;
+  const int64_t b0 = l0 + len * blockIdx.y / kPostParts, b1 = l0 + len * (blockIdx.y + 1) / kPostParts;
   constexpr int kStep = kPostWarps * 32 * kPostUnroll;
+  int seen = 0;   // the leader's count as this warp last saw it
   for (int64_t b = b0 + (threadIdx.x >> 5) * 32 * kPostUnroll; b < b1; b += kStep) {
-    if (*(volatile int *)&s_cnt > cap) break;   // full: the count is already past cap
+    if (seen > cap) break;   // full: the count is already past cap
     int32_t u[kPostUnroll];
     uint64_t a[kPostUnroll];
 #pragma unroll
@@ -164,16 +167,24 @@ gather_postings_kernel(DevIndex ix, const jag_filter *filters, const int32_t *le
       const uint32_t m = __ballot_sync(kFull, pass);
       if (!m) continue;
       int off = 0;
-      if (lane == 0) off = atomicAdd(&s_cnt, __popc(m));
+      if (lane == 0) off = atomicAdd(counts + qi, __popc(m));
       off = __shfl_sync(kFull, off, 0);
+      seen = off + __popc(m);
       if (pass) {
         const int64_t pos = off + __popc(m & lanemask_lt());
         if (pos < cap) lists[qi * cap + pos] = u[r];
       }
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) counts[qi] = s_cnt > cap ? (int32_t)cap + 1 : s_cnt;
+}
+
+// The leader's count past cap is only known to exceed it: it reads cap + 1.
+__global__ void clamp_counts_kernel(const int32_t *leaders, const unsigned long long *nlead, int64_t cap,
+                                    int32_t *counts) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (int64_t)nlead[0]) return;
+  const int64_t qi = leaders[w];
+  if (counts[qi] > cap) counts[qi] = (int32_t)cap + 1;
 }
 
 // K2b: one pass over a tile of masks evaluates the predicates of up to
@@ -830,8 +841,10 @@ cudaError_t run_search(const SearchLaunch &L) {
                                                 (uint32_t)(L.lgroup.slots - 1), L.lgroup.lslot);
     list_leader_kernel<<<qb, 256, 0, L.stream>>>(L.plans, L.filters, L.nq, L.lgroup.hlead, L.lgroup.lslot,
                                                  L.lgroup.leaders, L.work + 8);
-    gather_postings_kernel<<<(unsigned)L.nq, kPostWarps * 32, 0, L.stream>>>(
+    gather_postings_kernel<<<dim3((unsigned)L.nq, kPostParts), kPostWarps * 32, 0, L.stream>>>(
         L.ix, L.filters, L.lgroup.leaders, L.work + 8, L.cap, L.lists, L.list_counts);
+    clamp_counts_kernel<<<(unsigned)((L.nq + 255) / 256), 256, 0, L.stream>>>(L.lgroup.leaders, L.work + 8, L.cap,
+                                                                           L.list_counts);
     // the other leaders sit at the back of the array, in reverse order: the
     // mask pass reads them as leaders[nq - 1 - i]
     dim3 grid((unsigned)((L.ix.n + kGatherTile - 1) / kGatherTile), (unsigned)((L.nq + kGatherQPB - 1) / kGatherQPB));
