@@ -440,8 +440,10 @@ def run_ours(args):
         "serving_form_10m": large,
         "serving": serving,
         "clocks": clk.summary(),
-        # per step: prep, graph search, scan work items, scan tiles, scan merge
-        "gpu_launches": int(args.steps * 5),
+        # per step (the launch list in profiles/): preparation, graph search, and
+        # the tensor-core scan's count, two sums, offsets, fill, items, query
+        # norms, contraction and selection
+        "gpu_launches": int(args.steps * 11),
     }
     if rank == 0:
         print(json.dumps(out))
